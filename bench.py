@@ -1,0 +1,362 @@
+"""Benchmark: the serving stream of Dual (O-)BDRS solves on one B300 (or N replicas).
+
+Workload (one "step"): a seeded stream of ``--requests`` OT solves with Poisson arrivals at
+``--rate`` requests/s, grid sizes drawn 50% 32x32, 35% 64x64, 15% 128x128, histogram classes drawn
+per request (uniform-random, 1-5 component Gaussian mixtures, Cauchy-like, 90%-sparse floored at
+1e-15), eps0 = 1, lambda = 1, FP32 exp / FP64 potentials, certificate every ``--cert-every``
+iterations, each request stopping at a 1% relative certified gap or ``--max-iters``.
+
+Metric: implicit entries per second over the whole stream (2 n m entries per iteration), with
+p50/p99 solve latency (arrival to completion) and time to certified gap beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank serves its own stream (independent replicas, weak scaling);
+the reference arm (the FP64 CPU oracle) runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ot_inputs as I  # noqa: E402
+
+METRIC = "implicit entries/s per dual sweep (serving stream); time to certified gap; p50/p99 solve latency"
+UNIT = "entries/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--engine", default="serial", choices=["serial"])
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=32.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--max-iters", type=int, default=2000)
+    ap.add_argument("--cert-every", type=int, default=100)
+    ap.add_argument("--tol-rel", type=float, default=0.01)
+    ap.add_argument("--seed", type=int, default=2609)
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks during the timed region (nvidia-smi sampling)
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------------------------
+def make_stream(args, rank: int):
+    reqs = I.serving_stream(args.requests, args.seed + 7919 * rank, args.rate)
+    probs = [I.request_problem(r) for r in reqs]
+    return reqs, probs
+
+
+def solve_params(args):
+    return dict(eps0=1.0, lam=1.0, max_iters=args.max_iters, cert_every=args.cert_every, precision="mufu",
+                tol_rel=args.tol_rel)
+
+
+def run_serial(ctx, reqs, probs, dev_inputs, args, host: bool):
+    """One-at-a-time FIFO serving: each request starts at max(arrival, previous completion)."""
+    import torch
+    t0 = time.perf_counter()
+    lat, ttg, entries, conv = [], [], 0.0, 0
+    h2d = d2h = 0
+    for r, p, dv in zip(reqs, probs, dev_inputs):
+        now = time.perf_counter() - t0
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        ts = time.perf_counter()
+        if host:
+            f, g, res = ctx.solve(p.x, p.y, p.a, p.b, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15,
+                                  **solve_params(args))
+            h2d += p.x.nbytes + p.y.nbytes + p.a.nbytes + p.b.nbytes
+            d2h += f.nbytes + g.nbytes
+        else:
+            x, y, a, b = dv
+            f, g, res = ctx.solve(x, y, a, b, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15,
+                                  **solve_params(args))
+        te = time.perf_counter()
+        lat.append(te - t0 - r.arrival_s)
+        ttg.append(te - ts)
+        entries += 2.0 * p.n * p.m * res["iters"]
+        conv += res["stop"] == "tol"
+    return dict(latency=lat, ttg=ttg, entries=entries, converged=conv, h2d=h2d, d2h=d2h)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+# ----------------------------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(args, reqs, probs, budget_s: float):
+    """The oracle as it stands (dense FP64 numpy) on a bounded sample of the stream: requests in
+    arrival order, each for up to --max-iters iterations with its certificates and stop rule,
+    until about budget_s seconds of CPU work.  Returns entries/s and what was sampled."""
+    import oracle as O
+    t0 = time.perf_counter()
+    entries = 0.0
+    done = []
+    for r, p in zip(reqs, probs):
+        if p.n > 4096:
+            continue  # the dense oracle needs n*m*8 bytes; the 128x128 class is left out of the sample
+        C = O.cost_matrix(p.x, p.y, p.kappa)
+        a = np.maximum(p.a, 1e-15)
+        a = a / a.sum()
+        b = np.maximum(p.b, 1e-15)
+        b = b / b.sum()
+        st = O.DualState.initial(p.n, p.m)
+        la, lb = np.log(a), np.log(b)
+        k = 0
+        while k < args.max_iters:
+            st = O.dual_obdrs_step(st, la, lb, C, 1.0, 1.0)
+            k += 1
+            entries += 2.0 * p.n * p.m
+            if args.cert_every > 0 and k % args.cert_every == 0:
+                cert = O.certificate_of(st, a, b, C, p.omega)
+                if (cert["U"] - cert["L"]) <= args.tol_rel * abs(cert["U"]):
+                    break
+            if time.perf_counter() - t0 > budget_s:
+                break
+        done.append(f"{p.n}:{k}")
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return entries / dt, dt, done
+
+
+def oracle_threads() -> int:
+    # the oracle's work is numpy element-wise exp/log/sum over dense arrays: one host thread
+    return 1
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    reqs, probs = make_stream(args, 0)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, dt, done = oracle_sample(args, reqs, probs, args.cpu_sample_s)
+        if i >= args.warmup:
+            vals.append((v, dt, done))
+    v = statistics.median([x[0] for x in vals])
+    sample = (f"oracle (dense FP64 numpy) on the stream's requests in arrival order, n <= 4096, "
+              f"~{args.cpu_sample_s:.0f} s per step; last step covered n:iters {vals[-1][2]}")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([x[1] for x in vals]),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "serving stream, mixed 32x32/64x64/128x128 grid histograms",
+                      "requests": args.requests, "rate_per_s": args.rate, "max_iters": args.max_iters,
+                      "tol_rel": args.tol_rel, "seed": args.seed},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------------
+def peaks_for_roofline(probe, clocks):
+    # entries/clk/SM bound: min(FP32 lanes / (d + 2), MUFU ex2 lanes); d = 2 for grid workloads
+    fp32 = 128.0
+    mufu = 32.0
+    per_clk = min(fp32 / 4.0, mufu)
+    mhz = clocks.get("sm_max_mhz") or 2032.0
+    return per_clk * 148 * mhz * 1e6
+
+
+def run_ours(args, rank: int, world: int):
+    import ctypes
+    import torch
+    import paper_2609_33814_b300 as P
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = P.Context(dev)
+    lib = P.lib()
+    reqs, probs = make_stream(args, rank)
+    dev_inputs = [(torch.from_numpy(p.x).cuda(), torch.from_numpy(p.y).cuda(), torch.from_numpy(p.a).cuda(),
+                   torch.from_numpy(p.b).cuda()) for p in probs]
+    l2buf = torch.empty(256 << 18, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+
+    for _ in range(args.warmup):
+        run_serial(ctx, reqs, probs, dev_inputs, args, host=False)
+        flush_l2(l2buf)
+    barrier()
+    clock = ClockSampler(dev)
+    clock.start()
+    lib.ot_profile_reset(ctx.handle)
+    lib.ot_profile_enable(ctx.handle, 1)
+    step_times, results = [], []
+    for _ in range(args.steps):
+        flush_l2(l2buf)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        res = run_serial(ctx, reqs, probs, dev_inputs, args, host=False)
+        ev1.record()
+        barrier()
+        step_times.append(ev0.elapsed_time(ev1) / 1e3)
+        results.append(res)
+    lib.ot_profile_enable(ctx.handle, 0)
+    clocks = clock.stop()
+    nl = ctypes.c_int64()
+    lib.ot_launch_count(ctx.handle, ctypes.byref(nl))
+    kst = []
+    for kind in range(4):
+        n = ctypes.c_int64()
+        e = ctypes.c_double()
+        ms = ctypes.c_double()
+        lib.ot_profile_read(ctx.handle, kind, ctypes.byref(n), ctypes.byref(e), ctypes.byref(ms))
+        kst.append((n.value, e.value, ms.value))
+    # end to end: host buffers through the C ABI, copies inside the timed region
+    e2e_times, e2e_res = [], []
+    for _ in range(args.steps):
+        flush_l2(l2buf)
+        barrier()
+        t = time.perf_counter()
+        r2 = run_serial(ctx, reqs, probs, dev_inputs, args, host=True)
+        barrier()
+        e2e_times.append(time.perf_counter() - t)
+        e2e_res.append(r2)
+
+    t_step = max(step_times)
+    entries = sum(r["entries"] for r in results) / len(results)
+    if dist:
+        tt = torch.tensor([t_step, entries, statistics.median(e2e_times), e2e_res[-1]["entries"]],
+                          dtype=torch.float64, device="cuda")
+        gathered = [torch.zeros_like(tt) for _ in range(world)]
+        td.all_gather(gathered, tt)
+        t_step = max(float(g[0]) for g in gathered)
+        entries_all = sum(float(g[1]) for g in gathered)
+        e2e_t = max(float(g[2]) for g in gathered)
+        e2e_entries = sum(float(g[3]) for g in gathered)
+    else:
+        entries_all = entries
+        e2e_t = statistics.median(e2e_times)
+        e2e_entries = e2e_res[-1]["entries"]
+    if rank != 0:
+        if dist:
+            td.barrier()
+        return
+    lat = results[-1]["latency"]
+    ttg = results[-1]["ttg"]
+    fast_n, fast_e, fast_ms = kst[0][0] + kst[1][0], kst[0][1] + kst[1][1], kst[0][2] + kst[1][2]
+    achieved = fast_e / (fast_ms / 1e3) if fast_ms > 0 else None
+    peak = peaks_for_roofline(None, clocks)
+    cpu_v, cpu_dt, cpu_done = oracle_sample(args, reqs, probs, args.cpu_sample_s)
+    out = {
+        "metric": METRIC, "value": entries_all / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 exp / f64 potentials", "data": "synthetic",
+        "config": {"workload": "serving stream, mixed 32x32/64x64/128x128 grid histograms",
+                   "requests": args.requests, "rate_per_s": args.rate, "max_iters": args.max_iters,
+                   "cert_every": args.cert_every, "tol_rel": args.tol_rel, "eps0": 1.0, "lambda": 1.0,
+                   "engine": args.engine, "seed": args.seed, "l2": "flushed between steps (256 MB write)"},
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "time_to_gap_median_s": float(np.median(ttg)), "time_to_gap_p99_s": float(np.percentile(ttg, 99)),
+        "converged_frac": results[-1]["converged"] / len(lat),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "entries/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "fast sweep (row + column launches)", "launches": fast_n,
+                     "avg_launch_ms": fast_ms / max(fast_n, 1),
+                     "peak_basis": "min(128 FP32 lanes / 4 ops, 32 MUFU ex2) per clk per SM x 148 SMs x sm_max_mhz"},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                         "sample": f"dense FP64 numpy oracle, stream requests with n <= 4096 in arrival order, "
+                                   f"{cpu_dt:.1f} s; n:iters {cpu_done}"},
+        "e2e": {"value": e2e_entries / e2e_t, "unit": UNIT,
+                "h2d_bytes_per_step": e2e_res[-1]["h2d"], "d2h_bytes_per_step": e2e_res[-1]["d2h"]},
+        "gpu_launches": int(nl.value),
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        td.barrier()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * ot.h - C ABI of the B300 (sm_103a) Dual (O-)BDRS optimal-transport solver.
+ *
+ * The library solves the unregularised discrete optimal-transport problem
+ *     p* = min <C, X>  over  X >= 0, X 1 = r, X^T 1 = c          (Sec. 2, Eq. unregularized_ot_primal)
+ * with the squared-Euclidean cost C_ij = kappa ||x_i - y_j||^2 between two point clouds, by the
+ * log-domain Dual O-BDRS iteration of Algorithm 1 (Prop. 2; lambda = 1 is Dual BDRS, Prop. 1),
+ * and certifies it with the primal-dual bounds L <= p* <= U of Proposition 3, whose upper bound is
+ * evaluated as in Algorithm 2.  The cost matrix, kernel and plan are never stored: every sweep
+ * recomputes C_ij in registers (linear memory, Sec. 3.2).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns ot_status and never throws or aborts.  OT_OK is success.
+ *   - Inputs are borrowed for the duration of the call; outputs go to caller-owned buffers.
+ *     Opaque handles are owned by the library and released by their *_destroy function.
+ *   - A context, and every state created from it, may be used by one thread at a time.
+ *   - Not reaching the requested tolerance is not an error: the result says why the run stopped.
+ *   - A non-finite value in the iteration gives OT_ENUMERIC; the state stays readable.
+ *   - A device wait that exceeds its bound gives OT_ETIMEDOUT; the state must then be recreated.
+ *   - Pointers in ot_problem are host pointers unless on_device = 1, in which case they are device
+ *     pointers of the context's GPU (for example the data pointers of CUDA torch tensors).
+ */
+#ifndef OT_B300_H
+#define OT_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ot_context ot_context;
+typedef struct ot_state ot_state;
+
+typedef enum {
+  OT_OK = 0,
+  OT_EINVAL = 1,      /* invalid argument (sizes, weights, lambda, eps0, null pointers) */
+  OT_ENOMEM = 2,      /* device or host allocation failed */
+  OT_ECUDA = 3,       /* a CUDA runtime call failed (see ot_last_error) */
+  OT_ENUMERIC = 4,    /* a potential or LSE became non-finite */
+  OT_ETIMEDOUT = 5,   /* a bounded device wait gave up */
+  OT_EBUSY = 6,       /* (serving) request not finished yet */
+  OT_ECANCELLED = 7,  /* (serving) request was cancelled */
+  OT_ENOTFOUND = 8    /* (serving) unknown request id */
+} ot_status;
+
+/* Arithmetic of the dual sweeps.  Certificate iterations always run compensated
+ * (float-float exponent) sweeps in the FP32 modes and FP64 sweeps in OT_FP64. */
+typedef enum {
+  OT_EXP_MUFU = 0,    /* FP32 exponent, MUFU exp2, FP64 potentials (the fast path) */
+  OT_EXP_POLY = 1,    /* FP32 exponent, exp2 by an FMA-pipe polynomial */
+  OT_EXP_SPLIT = 2,   /* FP32 exponent, exp2 split between MUFU and the polynomial */
+  OT_FP64 = 3,        /* FP64 exponent, exp2 and sums */
+  OT_FP32_COMP = 4    /* compensated float-float exponent on every iteration */
+} ot_precision;
+
+typedef enum {
+  OT_STOP_TOL = 0,        /* U_best - L_best <= tol_abs or (U_best - L_best) / U_best <= tol_rel */
+  OT_STOP_MAX_ITERS = 1,  /* max_iters iterations done */
+  OT_STOP_TIME = 2,       /* time_budget_s exceeded (checked after each certificate) */
+  OT_STOP_NONE = 3        /* ot_step: ran the requested iterations */
+} ot_stop_reason;
+
+/* Vectors of the state (Algorithm 1's return tuple and the certificate potentials). */
+typedef enum {
+  OT_LOG_ALPHA = 0,       /* log alpha^k              (n) */
+  OT_LOG_ALPHA_HAT = 1,   /* log alpha-hat^k          (n) */
+  OT_LOG_BETA = 2,        /* log beta^k               (m) */
+  OT_LOG_BETA_PREV = 3,   /* log beta^{k-1}           (m) */
+  OT_LOG_BETA_HAT = 4,    /* log beta-hat^k           (m) */
+  OT_LOG_BETA_TILDE = 5,  /* log beta-tilde^{k-1}     (m) */
+  OT_F_CERT = 6,          /* f = eps log A of the latest certificate            (n) */
+  OT_G_CERT = 7,          /* g = eps log(B / c) of the latest certificate        (m) */
+  OT_F_BEST = 8,          /* f of the certificate with the lowest relative gap  (n) */
+  OT_G_BEST = 9           /* g of that certificate                               (m) */
+} ot_vector;
+
+/* The problem of Sec. 2: sources x (n x d, row-major) with weights a (the paper's r), targets
+ * y (m x d) with weights b (the paper's c).  Weights must be finite and > 0 (or >= 0 with a
+ * zero_mass_floor > 0, the paper's treatment of zero-mass pixels, App. G); they are renormalised
+ * to total mass one in FP64.  d is 1, 2 or 3; n, m >= 1 and < 2^31.
+ * cost_scale = kappa > 0, or 0 to use kappa = 1 / max_ij ||x_i - y_j||^2 (App. G colour cost).
+ * omega >= osc(C) bounds the cost range in U = <t,w> + omega delta (Prop. 3); 0 computes
+ * kappa (max - min) of the pair distances on the device. */
+typedef struct {
+  int64_t n, m;
+  int32_t d;
+  int32_t on_device;
+  const float* x;
+  const float* y;
+  const double* a;
+  const double* b;
+  double cost_scale;
+  double omega;
+  double zero_mass_floor;
+} ot_problem;
+
+/* Algorithm 1's parameters: eps0 = eta > 0, lambda in [1, 2) (O-BDRS overrelaxation; 1 = BDRS).
+ * cert_every > 0 evaluates Prop. 3 after every cert_every-th iteration; 0 never.
+ * stream: a cudaStream_t to run on (0 = the context's own stream). */
+typedef struct {
+  double eps0;
+  double lambda;
+  int64_t max_iters;
+  double time_budget_s;   /* <= 0: no time budget */
+  int32_t cert_every;
+  int32_t precision;      /* ot_precision */
+  double tol_abs;         /* <= 0: unused */
+  double tol_rel;         /* <= 0: unused */
+  uint64_t stream;
+} ot_params;
+
+/* Outcome of a solve or a run of steps.  U, L are the bounds of the latest certificate,
+ * U_best = min_t U_t and L_best = max_t L_t over all certificates so far (App. G.3);
+ * gap_abs = U_best - L_best, gap_rel = gap_abs / U_best; best_iter is the certificate iteration
+ * with the lowest relative gap (U_t - L_t) / U_t, whose potentials ot_solve returns. */
+typedef struct {
+  int64_t iters;
+  int64_t best_iter;
+  int64_t n_certs;
+  double U, L, U_best, L_best, gap_abs, gap_rel;
+  double eps_final;
+  double elapsed_s;
+  double kappa;
+  double omega;
+  int32_t stop;           /* ot_stop_reason */
+  int32_t device_errors;  /* raw device error bits (0 when OT_OK) */
+} ot_result;
+
+/* Sensible defaults: eps0 = 1, lambda = 1, max_iters = 1000, cert_every = 100, OT_EXP_MUFU. */
+void ot_params_default(ot_params* p);
+
+/* Create a context on CUDA device `device` (it owns a stream and the kernel launch plans). */
+ot_status ot_context_create(int device, ot_context** out);
+void ot_context_destroy(ot_context* ctx);
+
+/* Text for a status code, and the last error message recorded on a context (never NULL). */
+const char* ot_status_str(ot_status s);
+const char* ot_last_error(const ot_context* ctx);
+
+/* Solve one problem with Algorithm 1 and periodic certificates until the stop rule, max_iters or
+ * the time budget.  f_out (n) and g_out (m), each optional (NULL), receive the certificate
+ * potentials f = eps log A, g = eps log(B/c) (Prop. 3, Eq. cert_dual_potentials) of the retained
+ * iterate, host or device memory as problem->on_device says.  Allocates and frees its state. */
+ot_status ot_solve(ot_context* ctx, const ot_problem* prob, const ot_params* params, double* f_out,
+                   double* g_out, ot_result* res);
+
+/* A resident solver state: Algorithm 1 initialised (log alpha^{-1} = log beta^{-1} =
+ * log beta^{-2} = 0, k = 0), inputs uploaded and packed.  The problem's arrays are copied. */
+ot_status ot_state_create(ot_context* ctx, const ot_problem* prob, const ot_params* params,
+                          ot_state** out);
+void ot_state_destroy(ot_state* st);
+
+/* Run exactly n_iters iterations of Algorithm 1 (no stop test).  Iteration k (0-based) is a
+ * certificate iteration when (k + 1) % cert_every == 0; its bounds update the result's best
+ * values.  res may be NULL. */
+ot_status ot_step(ot_state* st, int64_t n_iters, ot_result* res);
+
+/* Certificate (Prop. 3 with Algorithm 2) of the last completed iteration k-1: the stored one if
+ * that iteration was a certificate iteration, else a standalone compensated (or FP64) pass over
+ * the state's log alpha-hat, log beta-hat, log beta-tilde.  Needs at least one iteration. */
+ot_status ot_certificate(ot_state* st, ot_result* res);
+
+/* Copy a state vector to host memory `out` (n or m doubles); *k receives the number of completed
+ * iterations.  Either output may be NULL. */
+ot_status ot_state_get(ot_state* st, int which, double* out, int64_t* k);
+
+/* Resume: overwrite a state vector from host memory and set the completed-iteration count to k.
+ * Only OT_LOG_ALPHA, OT_LOG_BETA and OT_LOG_BETA_PREV may be set (the inputs of iteration k);
+ * the column operands of iteration k are rebuilt from them. */
+ot_status ot_state_set(ot_state* st, int which, const double* in, int64_t k);
+
+/* The (kappa, omega) the state uses, after any device-side cost-range pass. */
+ot_status ot_state_cost(ot_state* st, double* kappa, double* omega);
+
+/* Measurement support (not part of the method): kernel timing.  While enabled on a context, every
+ * iteration chunk of its states records a CUDA event on the launching stream before and after each
+ * sweep launch (inside the captured CUDA graph) and waits for the chunk, and per kind of sweep
+ * (0 fast row, 1 fast column, 2 certificate row, 3 certificate column) the number of launches,
+ * the algorithmic implicit entries (n * m per sweep) and the summed event durations (ms) accumulate.
+ * Any output pointer may be NULL. */
+ot_status ot_profile_enable(ot_context* ctx, int on);
+ot_status ot_profile_reset(ot_context* ctx);
+ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* entries, double* ms);
+
+/* Number of CUDA kernels this context has launched since creation or the last ot_profile_reset
+ * (every node of a replayed CUDA graph counts). */
+ot_status ot_launch_count(ot_context* ctx, int64_t* launches);
+
+/* Measurement support (not part of the method): pipe-throughput microbenchmarks on `device`
+ * used to derive the sweep's roofline.  For probe k = 0..5 (MUFU ex2, FFMA, FFMA2, three-input
+ * FMNMX, a 1 ex2 : 4 FMA : 1 FADD mix, FADD), out[2k] receives lane operations per clock per SM
+ * (for the mix: exp2 per clock per SM) and out[2k+1] the SM clock in MHz seen during the probe.
+ * nout >= 12; iters >= 1 sets the loop length (10^4 .. 10^5 is typical). */
+ot_status ot_probe_pipes(int device, int iters, double* out, int nout);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OT_B300_H */

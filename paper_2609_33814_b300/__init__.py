@@ -1,0 +1,255 @@
+"""Python binding of the B300 Dual (O-)BDRS optimal-transport solver.
+
+A thin ctypes layer over the C ABI in ``include/ot.h`` (``libot.so``, built in-tree by
+``paper_2609_33814_b300.build``): argument marshalling only.  Every step of the solver
+runs in the library's CUDA kernels; there is no CPU fallback, and importing the
+package fails loudly when the shared library is missing.
+
+Inputs may be numpy arrays (host) or CUDA torch tensors (device pointers are passed
+through, ``on_device = 1``).  Point clouds are float32 ``(n, d)``, weights float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libot.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2609_33814_b300.build` "
+        "(the solver has no CPU fallback)")
+
+_lib = C.CDLL(LIB_PATH)
+
+# --- enums (mirror include/ot.h) ----------------------------------------------------------
+OT_OK, OT_EINVAL, OT_ENOMEM, OT_ECUDA, OT_ENUMERIC, OT_ETIMEDOUT, OT_EBUSY, OT_ECANCELLED, OT_ENOTFOUND = range(9)
+OT_EXP_MUFU, OT_EXP_POLY, OT_EXP_SPLIT, OT_FP64, OT_FP32_COMP = range(5)
+OT_STOP_TOL, OT_STOP_MAX_ITERS, OT_STOP_TIME, OT_STOP_NONE = range(4)
+(OT_LOG_ALPHA, OT_LOG_ALPHA_HAT, OT_LOG_BETA, OT_LOG_BETA_PREV, OT_LOG_BETA_HAT, OT_LOG_BETA_TILDE,
+ OT_F_CERT, OT_G_CERT, OT_F_BEST, OT_G_BEST) = range(10)
+
+PRECISIONS = {"mufu": OT_EXP_MUFU, "poly": OT_EXP_POLY, "split": OT_EXP_SPLIT, "fp64": OT_FP64,
+              "comp": OT_FP32_COMP}
+STOP_NAMES = {OT_STOP_TOL: "tol", OT_STOP_MAX_ITERS: "max_iters", OT_STOP_TIME: "time", OT_STOP_NONE: "none"}
+
+
+class OtProblem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("m", C.c_int64), ("d", C.c_int32), ("on_device", C.c_int32),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("a", C.c_void_p), ("b", C.c_void_p),
+                ("cost_scale", C.c_double), ("omega", C.c_double), ("zero_mass_floor", C.c_double)]
+
+
+class OtParams(C.Structure):
+    _fields_ = [("eps0", C.c_double), ("lam", C.c_double), ("max_iters", C.c_int64),
+                ("time_budget_s", C.c_double), ("cert_every", C.c_int32), ("precision", C.c_int32),
+                ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("stream", C.c_uint64)]
+
+
+class OtResult(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("best_iter", C.c_int64), ("n_certs", C.c_int64),
+                ("U", C.c_double), ("L", C.c_double), ("U_best", C.c_double), ("L_best", C.c_double),
+                ("gap_abs", C.c_double), ("gap_rel", C.c_double), ("eps_final", C.c_double),
+                ("elapsed_s", C.c_double), ("kappa", C.c_double), ("omega", C.c_double),
+                ("stop", C.c_int32), ("device_errors", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["stop"] = STOP_NAMES.get(self.stop, self.stop)
+        return d
+
+
+_P = C.c_void_p
+_lib.ot_params_default.argtypes = [C.POINTER(OtParams)]
+_lib.ot_status_str.restype = C.c_char_p
+_lib.ot_status_str.argtypes = [C.c_int]
+_lib.ot_last_error.restype = C.c_char_p
+_lib.ot_last_error.argtypes = [_P]
+_lib.ot_context_create.argtypes = [C.c_int, C.POINTER(_P)]
+_lib.ot_context_destroy.argtypes = [_P]
+_lib.ot_solve.argtypes = [_P, C.POINTER(OtProblem), C.POINTER(OtParams), _P, _P, C.POINTER(OtResult)]
+_lib.ot_state_create.argtypes = [_P, C.POINTER(OtProblem), C.POINTER(OtParams), C.POINTER(_P)]
+_lib.ot_state_destroy.argtypes = [_P]
+_lib.ot_step.argtypes = [_P, C.c_int64, C.POINTER(OtResult)]
+_lib.ot_certificate.argtypes = [_P, C.POINTER(OtResult)]
+_lib.ot_state_get.argtypes = [_P, C.c_int, _P, C.POINTER(C.c_int64)]
+_lib.ot_state_set.argtypes = [_P, C.c_int, _P, C.c_int64]
+_lib.ot_state_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+
+
+class OTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.ot_status_str(status).decode()}: {msg}")
+        self.status = status
+
+
+def lib() -> C.CDLL:
+    """The loaded ``libot.so`` (for callers that use the C ABI directly)."""
+    return _lib
+
+
+# --- argument marshalling -----------------------------------------------------------------
+def _is_torch(t) -> bool:
+    return type(t).__module__.startswith("torch")
+
+
+def _host(arr, dtype) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(arr, dtype=dtype))
+
+
+def _ptr(arr) -> int:
+    if _is_torch(arr):
+        return int(arr.data_ptr())
+    return int(arr.ctypes.data)
+
+
+def make_problem(x, y, a, b, cost_scale: float = 0.0, omega: float = 0.0, zero_mass_floor: float = 0.0):
+    """Build an ``ot_problem``.  Returns (struct, keepalive) — keep the second alive during calls."""
+    dev = _is_torch(x)
+    if dev:
+        import torch
+        x = x.to(torch.float32).contiguous()
+        y = y.to(torch.float32).contiguous()
+        a = a.to(torch.float64).contiguous()
+        b = b.to(torch.float64).contiguous()
+        n, d = (int(x.shape[0]), int(x.shape[1])) if x.dim() == 2 else (int(x.shape[0]), 1)
+        m = int(y.shape[0])
+    else:
+        x = _host(x, np.float32)
+        y = _host(y, np.float32)
+        a = _host(a, np.float64)
+        b = _host(b, np.float64)
+        n, d = (x.shape[0], x.shape[1]) if x.ndim == 2 else (x.shape[0], 1)
+        m = y.shape[0]
+    p = OtProblem(n, m, d, 1 if dev else 0, _ptr(x), _ptr(y), _ptr(a), _ptr(b),
+                  float(cost_scale), float(omega), float(zero_mass_floor))
+    return p, (x, y, a, b)
+
+
+def make_params(eps0=1.0, lam=1.0, max_iters=1000, cert_every=100, precision="mufu", tol_abs=0.0,
+                tol_rel=0.0, time_budget_s=0.0, stream: int = 0) -> OtParams:
+    prm = OtParams()
+    _lib.ot_params_default(C.byref(prm))
+    prm.eps0 = float(eps0)
+    prm.lam = float(lam)
+    prm.max_iters = int(max_iters)
+    prm.cert_every = int(cert_every)
+    prm.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    prm.tol_abs = float(tol_abs)
+    prm.tol_rel = float(tol_rel)
+    prm.time_budget_s = float(time_budget_s)
+    prm.stream = int(stream)
+    return prm
+
+
+class Context:
+    """A solver context on one CUDA device (owns a stream)."""
+
+    def __init__(self, device: int = 0):
+        h = _P()
+        st = _lib.ot_context_create(int(device), C.byref(h))
+        if st != OT_OK:
+            raise OTError(st, f"ot_context_create({device})")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def last_error(self) -> str:
+        return _lib.ot_last_error(self._h).decode()
+
+    def check(self, st: int, what: str):
+        if st != OT_OK:
+            raise OTError(st, f"{what}: {self.last_error()}")
+
+    def close(self):
+        if self._h:
+            _lib.ot_context_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, x, y, a, b, cost_scale=0.0, omega=0.0, zero_mass_floor=0.0, **params):
+        """``ot_solve``: returns (f, g, result dict) — f, g numpy (host inputs) or torch (device inputs)."""
+        prob, keep = make_problem(x, y, a, b, cost_scale, omega, zero_mass_floor)
+        prm = make_params(**params)
+        if prob.on_device:
+            import torch
+            f = torch.empty(prob.n, dtype=torch.float64, device=keep[0].device)
+            g = torch.empty(prob.m, dtype=torch.float64, device=keep[0].device)
+        else:
+            f = np.empty(prob.n, np.float64)
+            g = np.empty(prob.m, np.float64)
+        res = OtResult()
+        self.check(_lib.ot_solve(self._h, C.byref(prob), C.byref(prm), _ptr(f), _ptr(g), C.byref(res)),
+                   "ot_solve")
+        return f, g, res.as_dict()
+
+    def state(self, x, y, a, b, cost_scale=0.0, omega=0.0, zero_mass_floor=0.0, **params) -> "State":
+        return State(self, x, y, a, b, cost_scale, omega, zero_mass_floor, **params)
+
+
+class State:
+    """A resident solver state (``ot_state_*``, ``ot_step``, ``ot_certificate``)."""
+
+    def __init__(self, ctx: Context, x, y, a, b, cost_scale=0.0, omega=0.0, zero_mass_floor=0.0, **params):
+        self.ctx = ctx
+        prob, keep = make_problem(x, y, a, b, cost_scale, omega, zero_mass_floor)
+        prm = make_params(**params)
+        h = _P()
+        ctx.check(_lib.ot_state_create(ctx.handle, C.byref(prob), C.byref(prm), C.byref(h)), "ot_state_create")
+        self._h = h
+        self.n, self.m = int(prob.n), int(prob.m)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ot_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n_iters: int) -> dict:
+        res = OtResult()
+        self.ctx.check(_lib.ot_step(self._h, int(n_iters), C.byref(res)), "ot_step")
+        return res.as_dict()
+
+    def certificate(self) -> dict:
+        res = OtResult()
+        self.ctx.check(_lib.ot_certificate(self._h, C.byref(res)), "ot_certificate")
+        return res.as_dict()
+
+    def get(self, which: int) -> np.ndarray:
+        ln = self.n if which in (OT_LOG_ALPHA, OT_LOG_ALPHA_HAT, OT_F_CERT, OT_F_BEST) else self.m
+        out = np.empty(ln, np.float64)
+        k = C.c_int64()
+        self.ctx.check(_lib.ot_state_get(self._h, int(which), out.ctypes.data, C.byref(k)), "ot_state_get")
+        return out
+
+    @property
+    def k(self) -> int:
+        k = C.c_int64()
+        self.ctx.check(_lib.ot_state_get(self._h, OT_LOG_ALPHA, None, C.byref(k)), "ot_state_get")
+        return int(k.value)
+
+    def set(self, which: int, values, k: int):
+        v = _host(values, np.float64)
+        self.ctx.check(_lib.ot_state_set(self._h, int(which), v.ctypes.data, int(k)), "ot_state_set")
+
+    def cost(self):
+        kap, om = C.c_double(), C.c_double()
+        self.ctx.check(_lib.ot_state_cost(self._h, C.byref(kap), C.byref(om)), "ot_state_cost")
+        return kap.value, om.value

@@ -1,0 +1,156 @@
+// Set-up kernels, launch helpers and the sweep dispatch table of the solver.
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "ot_sweep.cuh"
+
+namespace ot {
+
+SweepFn get_sweep_d1(int mode, int R, int ch, int v);
+SweepFn get_sweep_d2(int mode, int R, int ch, int v);
+SweepFn get_sweep_d3(int mode, int R, int ch, int v);
+
+// ---------------------------------------------------------------------------------------------
+// Set-up kernels
+// ---------------------------------------------------------------------------------------------
+
+// Coordinates into the tile-blocked pack (padding: coords 0, h = kPadH), kappa ||.||^2 in FP64.
+__global__ void pack_coords_kernel(const float* __restrict__ pts, int npts, int d, int tiles, double kappa,
+                                   float* __restrict__ pack, double* __restrict__ n2) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= tiles * kTQ) return;
+  double s = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const float v = p < npts ? pts[(size_t)p * d + k] : 0.0f;
+    pack[pack_idx(p, k)] = v;
+    s += (double)v * (double)v;
+  }
+  for (int k = d; k < kNComp; ++k) pack[pack_idx(p, k)] = (k == d && p >= npts) ? kPadH : 0.0f;
+  if (p < npts) n2[p] = kappa * s;
+}
+
+// Deterministic single-CTA normalisation of weights: w / sum(w), optional floor for zero masses,
+// log w.  Sets err bit kErrNonFinite on a non-positive or non-finite weight.
+__global__ void normalise_weights_kernel(const double* __restrict__ w, int npts, double floor_mass,
+                                         double* __restrict__ wn, double* __restrict__ logw, int* err) {
+  __shared__ double red[kThreads];
+  const int tid = threadIdx.x;
+  double s = 0.0;
+  bool bad = false;
+  for (int i = tid; i < npts; i += kThreads) {
+    double v = w[i];
+    if (floor_mass > 0.0 && v < floor_mass && v >= 0.0) v = floor_mass;
+    bad |= !(v > 0.0) || !isfinite(v);
+    s += v;
+  }
+  const double tot = block_sum(s, red);
+  for (int i = tid; i < npts; i += kThreads) {
+    double v = w[i];
+    if (floor_mass > 0.0 && v < floor_mass && v >= 0.0) v = floor_mass;
+    const double q = v / tot;
+    wn[i] = q;
+    logw[i] = log(q);
+  }
+  if (bad) atomicOr(err, kErrNonFinite);
+}
+
+// Column pack for iteration k from log beta^{k-1}, log beta^{k-2}:
+// beta-tilde^{k-1} = beta^{k-1} + (beta^{k-1} - beta^{k-2}) / lambda (Algorithm 1 momentum).
+__global__ void repack_cols_kernel(const Inst* __restrict__ I) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= I->m) return;
+  const double eps = eps_of(I, *I->k);
+  const double b1 = I->log_beta[j], b2 = I->log_beta_prev[j];
+  const double tn = b1 + (b1 - b2) / I->lambda;
+  I->log_beta_tilde_next[j] = tn;
+  store_h(I->ypack, j, I->d, (tn - I->yn2[j] / eps) * kLog2e);
+}
+
+// max and min of ||x_i - y_j||^2 over all pairs (FP32, one launch, any grid size).
+__global__ void pair_cost_range_kernel(const float* __restrict__ x, int n, const float* __restrict__ y, int m,
+                                       int d, unsigned* __restrict__ out_max, unsigned* __restrict__ out_min) {
+  __shared__ float ys[3][256];
+  float mx = 0.0f, mn = FLT_MAX;
+  for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    float xi[3] = {0, 0, 0};
+    if (i < n)
+      for (int k = 0; k < d; ++k) xi[k] = x[(size_t)i * d + k];
+    for (int j0 = 0; j0 < m; j0 += 256) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+        const int j = j0 + t;
+        for (int k = 0; k < 3; ++k) ys[k][t] = (j < m && k < d) ? y[(size_t)j * d + k] : 0.0f;
+      }
+      __syncthreads();
+      if (i < n) {
+        const int jn = min(256, m - j0);
+        for (int t = 0; t < jn; ++t) {
+          float s = 0.0f;
+          for (int k = 0; k < 3; ++k) {
+            const float df = xi[k] - ys[k][t];
+            s = fmaf(df, df, s);
+          }
+          mx = fmaxf(mx, s);
+          mn = fminf(mn, s);
+        }
+      }
+    }
+  }
+  // non-negative floats order like their bit patterns
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out_max, __float_as_uint(mx));
+    atomicMin(out_min, __float_as_uint(mn));
+  }
+}
+
+// Sweep kernel for dimension d, precision mode, points per thread R, chunk width ch and variant
+// (0 row, 1 column, 2 column + certificate, 3 standalone certificate, 4 row + certificate).
+SweepFn get_sweep(int d, int mode, int R, int ch, int variant) {
+  switch (d) {
+    case 1: return get_sweep_d1(mode, R, ch, variant);
+    case 2: return get_sweep_d2(mode, R, ch, variant);
+    case 3: return get_sweep_d3(mode, R, ch, variant);
+  }
+  return nullptr;
+}
+size_t sweep_smem_bytes() { return (size_t)kStages * kStageTiles * kNComp * kTQ * sizeof(float); }
+
+cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
+                         cudaStream_t stream) {
+  if (nitems <= 0) return cudaSuccess;
+  void* args[] = {(void*)&insts, (void*)&items, (void*)&nitems};
+  return cudaLaunchKernel((const void*)fn, dim3(grid), dim3(kThreads), args, sweep_smem_bytes(), stream);
+}
+
+cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
+                               double* n2, cudaStream_t s) {
+  const int tot = tiles * kTQ;
+  pack_coords_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pts, npts, d, tiles, kappa, pack, n2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw, int* err,
+                             cudaStream_t s) {
+  normalise_weights_kernel<<<1, kThreads, 0, s>>>(w, npts, floor_mass, wn, logw, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_repack_cols(const Inst* I, int m, cudaStream_t s) {
+  repack_cols_kernel<<<(m + 255) / 256, 256, 0, s>>>(I);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_cost_range(const float* x, int n, const float* y, int m, int d, unsigned* mx,
+                                   unsigned* mn, int sms, cudaStream_t s) {
+  const int blocks = min((n + 255) / 256, sms * 8);
+  pair_cost_range_kernel<<<blocks, 256, 0, s>>>(x, n, y, m, d, mx, mn);
+  return cudaGetLastError();
+}
+
+}  // namespace ot

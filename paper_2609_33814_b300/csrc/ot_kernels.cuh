@@ -1,0 +1,72 @@
+// Shared definitions between the sweep kernels and the host runtime.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ot {
+
+constexpr int kThreads = 128;  // threads per CTA in every sweep kernel
+constexpr int kTQ = 128;       // points per shared-memory tile (per pipeline stage)
+constexpr int kStages = 4;     // TMA pipeline depth
+constexpr int kStageTiles = 2; // pack tiles per pipeline stage (one bulk copy, one CTA barrier)
+constexpr int kNComp = 5;      // pack components per point: up to 3 coords, h (hi), h (lo)
+constexpr uint32_t kWaitLimit = 1u << 26;  // mbarrier polls before a sweep gives up (~seconds)
+
+// Error bits written to Inst::err by device code.
+enum : int { kErrTimeout = 1, kErrNonFinite = 2 };
+
+// Exp2 implementations of the FP32 sweep.
+enum : int { kExpMufu = 0, kExpPoly = 1, kExpSplit = 2 };
+
+// Precision of one sweep launch.
+enum : int { kSweepFast = 0, kSweepComp = 1, kSweepF64 = 2 };
+
+// Certificate record layout (doubles) written by the last CTA of a certificate iteration.
+enum : int {
+  kCertIter = 0, kCertEps, kCertU, kCertL, kCertDelta, kCertCostZ, kCertRF, kCertCG, kCertLen = 8
+};
+
+// One OT instance as the kernels see it.  All device pointers are owned by the runtime.
+//
+// Packs are tile-blocked structure-of-arrays: point p lives in tile p / kTQ at offset p % kTQ,
+// and tile t holds kNComp rows of kTQ floats: coords 0..d-1, then h (hi), then h (lo).
+// The coordinates are the caller's float32 points; h is the per-point offset of the
+// exponent in base 2 (see the sweep kernels), rewritten by every epilogue.
+struct Inst {
+  int n, m, d;
+  int tiles_x, tiles_y;          // ceil(n / kTQ), ceil(m / kTQ)
+  int pblk_x;                    // point blocks of the certificate row sweep (layout of blk)
+  double kappa, eta, lambda, omega;
+  float* xpack;                  // [tiles_x][kNComp][kTQ]
+  float* ypack;                  // [tiles_y][kNComp][kTQ]
+  const double* a;               // source weights r (normalised)
+  const double* b;               // target weights c (normalised)
+  const double* log_a;           // log r
+  const double* log_b;           // log c
+  const double* xn2;             // kappa * ||x_i||^2
+  const double* yn2;             // kappa * ||y_j||^2
+  double* log_alpha;             // alpha^{k-1} -> alpha^k
+  double* log_alpha_hat;         // alpha-hat^k
+  double* log_beta;              // beta^{k-1} -> beta^k
+  double* log_beta_prev;         // beta^{k-2} -> beta^{k-1}
+  double* log_beta_hat;          // beta-hat^k
+  double* log_beta_tilde;        // beta-tilde^{k-1} used by the last completed iteration
+  double* log_beta_tilde_next;   // beta-tilde^{k} for the next iteration (packed into ypack)
+  double* f_cur;                 // certificate potentials of the latest certificate iteration
+  double* g_cur;
+  void* part;                    // split partials (float4 or double4 per point and split)
+  unsigned* cnt;                 // per point-block arrival counters (sized for R = 1)
+  unsigned* done;                // per-instance epilogue counter
+  double* blk;                   // certificate partial sums: pblk_x row blocks, then 3 per column block
+  long long* k;                  // completed iterations
+  double* cert;                  // certificate record (kCertLen doubles)
+  int* err;                      // error bits
+};
+
+// A unit of sweep work: instance, point block, split of the other side, and the split count of
+// that instance in this launch (the point-block size is kThreads * R of the launched kernel).
+struct Item {
+  int inst, pblk, split, nsplit;
+};
+
+}  // namespace ot

@@ -1,0 +1,792 @@
+// Host runtime of the solver: validation, device buffers, launch plans, CUDA graphs of iteration
+// chunks, certificate read-back with best-so-far bounds and the stop rule (Algorithm 1 with the
+// certificate of Proposition 3 every cert_every iterations; best bounds as in App. G.3).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ot.h"
+#include "ot_kernels.cuh"
+#include "ot_runtime.h"
+
+namespace ot {
+
+size_t sweep_smem_bytes();
+cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
+                         cudaStream_t stream);
+cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
+                               double* n2, cudaStream_t s);
+cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw, int* err,
+                             cudaStream_t s);
+cudaError_t launch_repack_cols(const Inst* I, int m, cudaStream_t s);
+cudaError_t launch_pair_cost_range(const float* x, int n, const float* y, int m, int d, unsigned* mx,
+                                   unsigned* mn, int sms, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------------
+void Context::set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  last_error = buf;
+}
+
+int Context::resident_ctas(SweepFn fn) {
+  auto it = occ.find((const void*)fn);
+  if (it != occ.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads, sweep_smem_bytes()) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int r = per_sm * sms;
+  occ[(const void*)fn] = r;
+  return r;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launch plans: points per thread R, chunk width and the split counts of both sweeps.
+// ---------------------------------------------------------------------------------------------
+static int split_count(int pblks, int qtiles, int target_items) {
+  int s = std::max(1, std::min(qtiles, (target_items + pblks - 1) / pblks));
+  const int tps = (qtiles + s - 1) / s;
+  return (qtiles + tps - 1) / tps;  // no empty split
+}
+
+static int env_int(const char* name, int dflt) {
+  const char* v = getenv(name);
+  return v && *v ? atoi(v) : dflt;
+}
+
+void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl) {
+  const int np = (int)std::max(in.n, in.m);
+  int R, ch = 8;
+  if (mode == kSweepF64) {
+    R = np >= ctx.sms * kThreads * 4 ? 2 : 1;
+  } else if (mode == kSweepComp) {
+    R = np >= ctx.sms * kThreads * 8 ? 4 : (np >= ctx.sms * kThreads * 2 ? 2 : 1);
+  } else {
+    R = np >= ctx.sms * kThreads * 8 ? 4 : (np >= ctx.sms * kThreads * 2 ? 2 : 1);
+    ch = R <= 2 ? 16 : 16;
+    // tuning overrides (experiments): OT_FORCE_R, OT_FORCE_CH
+    R = env_int("OT_FORCE_R", R);
+    ch = env_int("OT_FORCE_CH", ch);
+  }
+  if (!get_sweep(in.d, mode, R, ch, 0)) {
+    R = 1;
+    ch = 16;
+  }
+  pl.mode = mode;
+  pl.R = R;
+  pl.ch = ch;
+  const int rpb = kThreads * R;
+  pl.pblk_row = (int)((in.n + rpb - 1) / rpb);
+  pl.pblk_col = (int)((in.m + rpb - 1) / rpb);
+  const int tiles_x = (int)((in.n + kTQ - 1) / kTQ), tiles_y = (int)((in.m + kTQ - 1) / kTQ);
+  SweepFn fn = get_sweep(in.d, mode, R, ch, 0);
+  const int resident = ctx.resident_ctas(fn);
+  const int target = env_int("OT_FORCE_ITEMS", 4 * resident);
+  const int fs = env_int("OT_FORCE_SPLITS", 0);
+  pl.splits_row = fs > 0 ? split_count(1, tiles_y, fs) : split_count(pl.pblk_row, tiles_y, target);
+  pl.splits_col = fs > 0 ? split_count(1, tiles_x, fs) : split_count(pl.pblk_col, tiles_x, target);
+  pl.n_row = pl.pblk_row * pl.splits_row;
+  pl.n_col = pl.pblk_col * pl.splits_col;
+  pl.grid_row = std::min(pl.n_row, resident);
+  pl.grid_col = std::min(pl.n_col, resident);
+}
+
+static void build_items(std::vector<Item>& out, int inst, int pblks, int splits) {
+  // split-major order: the CTAs of one wave cover many point blocks of the same splits
+  for (int s = 0; s < splits; ++s)
+    for (int b = 0; b < pblks; ++b) out.push_back(Item{inst, b, s, splits});
+}
+
+// ---------------------------------------------------------------------------------------------
+// Instance: device buffers and set-up
+// ---------------------------------------------------------------------------------------------
+struct Carve {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    const size_t o = (off + 255) & ~(size_t)255;
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+#define OT_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      ctx.set_error("%s failed: %s", #call, cudaGetErrorString(e_));                 \
+      return OT_ECUDA;                                                                \
+    }                                                                                 \
+  } while (0)
+
+static int sweep_mode_of(int precision) {
+  if (precision == OT_FP64) return kSweepF64;
+  if (precision == OT_FP32_COMP) return kSweepComp;
+  return kSweepFast;
+}
+
+ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q) {
+  if (!p || !q) {
+    ctx.set_error("null problem or params");
+    return OT_EINVAL;
+  }
+  if (p->n < 1 || p->m < 1 || p->n >= (1ll << 31) - kTQ || p->m >= (1ll << 31) - kTQ) {
+    ctx.set_error("sizes must satisfy 1 <= n, m < 2^31 (got n=%lld m=%lld)", (long long)p->n, (long long)p->m);
+    return OT_EINVAL;
+  }
+  if (p->d < 1 || p->d > 3) {
+    ctx.set_error("d must be 1, 2 or 3 (got %d)", p->d);
+    return OT_EINVAL;
+  }
+  if (!p->x || !p->y || !p->a || !p->b) {
+    ctx.set_error("null x, y, a or b");
+    return OT_EINVAL;
+  }
+  if (!(p->cost_scale >= 0.0) || !std::isfinite(p->cost_scale) || !(p->omega >= 0.0) || !std::isfinite(p->omega) ||
+      !(p->zero_mass_floor >= 0.0)) {
+    ctx.set_error("cost_scale, omega and zero_mass_floor must be finite and >= 0");
+    return OT_EINVAL;
+  }
+  if (!(q->eps0 > 0.0) || !std::isfinite(q->eps0)) {
+    ctx.set_error("eps0 must be finite and > 0");
+    return OT_EINVAL;
+  }
+  if (!(q->lambda >= 1.0 && q->lambda < 2.0)) {
+    ctx.set_error("lambda must lie in [1, 2) (got %g)", q->lambda);
+    return OT_EINVAL;
+  }
+  if (q->max_iters < 0 || q->cert_every < 0) {
+    ctx.set_error("max_iters and cert_every must be >= 0");
+    return OT_EINVAL;
+  }
+  if (q->precision != OT_EXP_MUFU && q->precision != OT_FP64 && q->precision != OT_FP32_COMP &&
+      q->precision != OT_EXP_POLY && q->precision != OT_EXP_SPLIT) {
+    ctx.set_error("unknown precision %d", q->precision);
+    return OT_EINVAL;
+  }
+  return OT_OK;
+}
+
+ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream) {
+  ot_status vs = validate(ctx, p, q);
+  if (vs != OT_OK) return vs;
+  in.n = p->n;
+  in.m = p->m;
+  in.d = p->d;
+  in.params = *q;
+  in.stream = stream;
+  in.sweep_mode = sweep_mode_of(q->precision);
+  in.cert_mode = q->precision == OT_FP64 ? kSweepF64 : kSweepComp;
+  in.exp_mode = q->precision == OT_EXP_POLY ? kExpPoly : (q->precision == OT_EXP_SPLIT ? kExpSplit : kExpMufu);
+  plan_launch(ctx, in, in.sweep_mode, in.fast);
+  plan_launch(ctx, in, in.cert_mode, in.cert);
+  Inst& h = in.h;
+  h.tiles_x = (int)((in.n + kTQ - 1) / kTQ);
+  h.tiles_y = (int)((in.m + kTQ - 1) / kTQ);
+  h.pblk_x = in.cert.pblk_row;
+  h.n = (int)in.n;
+  h.m = (int)in.m;
+  h.d = in.d;
+  h.eta = q->eps0;
+  h.lambda = q->lambda;
+
+  const size_t n = in.n, m = in.m;
+  size_t nsp = 0;
+  for (const LaunchPlan* pl : {&in.fast, &in.cert})
+    nsp = std::max(nsp, std::max((size_t)pl->splits_row * n, (size_t)pl->splits_col * m));
+  const size_t maxblk = (std::max(n, m) + kThreads - 1) / kThreads;
+  Carve cv;
+  const size_t o_xpack = cv.take<float>((size_t)h.tiles_x * kNComp * kTQ);
+  const size_t o_ypack = cv.take<float>((size_t)h.tiles_y * kNComp * kTQ);
+  const size_t o_xraw = cv.take<float>(n * in.d);
+  const size_t o_yraw = cv.take<float>(m * in.d);
+  const size_t o_a = cv.take<double>(n), o_b = cv.take<double>(m);
+  const size_t o_ain = cv.take<double>(n), o_bin = cv.take<double>(m);
+  const size_t o_la = cv.take<double>(n), o_lb = cv.take<double>(m);
+  const size_t o_xn2 = cv.take<double>(n), o_yn2 = cv.take<double>(m);
+  const size_t o_state0 = cv.take<double>(2 * n + 5 * m);  // alpha, alpha_hat, beta, beta_prev, beta_hat, tilde, tilde_next
+  const size_t o_fg = cv.take<double>(2 * (n + m));         // f_cur, g_cur, f_best, g_best
+  const size_t o_part = cv.take<double4>(nsp);
+  const size_t o_cnt = cv.take<unsigned>(maxblk + 1);
+  const size_t o_blk = cv.take<double>((n + kThreads - 1) / kThreads + 3 * ((m + kThreads - 1) / kThreads));
+  const size_t o_ctrl = cv.take<double>(16);
+  const size_t o_range = cv.take<unsigned>(2);
+  const size_t o_inst = cv.take<Inst>(1);
+  const size_t n_items = (size_t)in.fast.n_row + in.fast.n_col + in.cert.n_row + in.cert.n_col;
+  const size_t o_items = cv.take<Item>(n_items);
+  in.bytes = cv.off;
+  if (cudaMalloc(&in.mem, in.bytes) != cudaSuccess) {
+    cudaGetLastError();
+    in.mem = nullptr;
+    ctx.set_error("cudaMalloc of %zu bytes failed", in.bytes);
+    return OT_ENOMEM;
+  }
+  char* base = (char*)in.mem;
+  h.xpack = (float*)(base + o_xpack);
+  h.ypack = (float*)(base + o_ypack);
+  in.xraw = (float*)(base + o_xraw);
+  in.yraw = (float*)(base + o_yraw);
+  h.a = (double*)(base + o_a);
+  h.b = (double*)(base + o_b);
+  double* ain = (double*)(base + o_ain);
+  double* bin = (double*)(base + o_bin);
+  h.log_a = (double*)(base + o_la);
+  h.log_b = (double*)(base + o_lb);
+  h.xn2 = (double*)(base + o_xn2);
+  h.yn2 = (double*)(base + o_yn2);
+  double* s0 = (double*)(base + o_state0);
+  h.log_alpha = s0;
+  h.log_alpha_hat = s0 + n;
+  h.log_beta = s0 + 2 * n;
+  h.log_beta_prev = s0 + 2 * n + m;
+  h.log_beta_hat = s0 + 2 * n + 2 * m;
+  h.log_beta_tilde = s0 + 2 * n + 3 * m;
+  h.log_beta_tilde_next = s0 + 2 * n + 4 * m;
+  double* fg = (double*)(base + o_fg);
+  h.f_cur = fg;
+  h.g_cur = fg + n;
+  in.f_best = fg + n + m;
+  in.g_best = fg + 2 * n + m;
+  h.part = base + o_part;
+  h.cnt = (unsigned*)(base + o_cnt);
+  h.done = h.cnt + maxblk;
+  h.blk = (double*)(base + o_blk);
+  double* ctrl = (double*)(base + o_ctrl);
+  h.cert = ctrl;
+  h.k = (long long*)(ctrl + 8);
+  h.err = (int*)(ctrl + 9);
+  in.ctrl = ctrl;
+  unsigned* range = (unsigned*)(base + o_range);
+  in.d_inst = (Inst*)(base + o_inst);
+  Item* items_base = (Item*)(base + o_items);
+  in.fast.d_row = items_base;
+  in.fast.d_col = in.fast.d_row + in.fast.n_row;
+  in.cert.d_row = in.fast.d_col + in.fast.n_col;
+  in.cert.d_col = in.cert.d_row + in.cert.n_row;
+
+  cudaStream_t s = stream;
+  OT_CUDA(cudaMemsetAsync(in.mem, 0, in.bytes, s));
+  const cudaMemcpyKind k_in = p->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  OT_CUDA(cudaMemcpyAsync(in.xraw, p->x, n * in.d * sizeof(float), k_in, s));
+  OT_CUDA(cudaMemcpyAsync(in.yraw, p->y, m * in.d * sizeof(float), k_in, s));
+  OT_CUDA(cudaMemcpyAsync(ain, p->a, n * sizeof(double), k_in, s));
+  OT_CUDA(cudaMemcpyAsync(bin, p->b, m * sizeof(double), k_in, s));
+
+  // cost scale and oscillation bound (App. G: kappa = 1 / max pair cost; omega >= osc(C))
+  double kappa = p->cost_scale, omega = p->omega;
+  if (kappa == 0.0 || omega == 0.0) {
+    const unsigned init[2] = {0u, 0x7f7fffffu};
+    OT_CUDA(cudaMemcpyAsync(range, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    OT_CUDA(launch_pair_cost_range(in.xraw, (int)n, in.yraw, (int)m, in.d, range, range + 1, ctx.sms, s));
+    ctx.launches += 1;
+    unsigned hr[2];
+    OT_CUDA(cudaMemcpyAsync(hr, range, sizeof(hr), cudaMemcpyDeviceToHost, s));
+    OT_CUDA(cudaStreamSynchronize(s));
+    float fmx, fmn;
+    memcpy(&fmx, &hr[0], 4);
+    memcpy(&fmn, &hr[1], 4);
+    if (kappa == 0.0) {
+      if (!(fmx > 0.0f)) {
+        ctx.set_error("all pair costs are zero: cost_scale must be given");
+        return OT_EINVAL;
+      }
+      kappa = 1.0 / (double)fmx;
+    }
+    if (omega == 0.0) omega = kappa * ((double)fmx - (double)fmn);
+    if (!(omega > 0.0)) omega = kappa * (double)fmx;
+  }
+  h.kappa = kappa;
+  h.omega = omega;
+  in.kappa = kappa;
+  in.omega = omega;
+
+  OT_CUDA(launch_pack_coords(in.xraw, (int)n, in.d, h.tiles_x, kappa, h.xpack, (double*)h.xn2, s));
+  OT_CUDA(launch_pack_coords(in.yraw, (int)m, in.d, h.tiles_y, kappa, h.ypack, (double*)h.yn2, s));
+  OT_CUDA(launch_normalise(ain, (int)n, p->zero_mass_floor, (double*)h.a, (double*)h.log_a, h.err, s));
+  OT_CUDA(launch_normalise(bin, (int)m, p->zero_mass_floor, (double*)h.b, (double*)h.log_b, h.err, s));
+  ctx.launches += 4;
+
+  std::vector<Item> items;
+  for (const LaunchPlan* pl : {&in.fast, &in.cert}) {
+    build_items(items, 0, pl->pblk_row, pl->splits_row);
+    build_items(items, 0, pl->pblk_col, pl->splits_col);
+  }
+  OT_CUDA(cudaMemcpyAsync(items_base, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, s));
+  OT_CUDA(cudaMemcpyAsync(in.d_inst, &h, sizeof(Inst), cudaMemcpyHostToDevice, s));
+  OT_CUDA(launch_repack_cols(in.d_inst, (int)m, s));
+  ctx.launches += 1;
+  if (cudaMallocHost(&in.h_ctrl, 16 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    in.h_ctrl = nullptr;
+    ctx.set_error("cudaMallocHost failed");
+    return OT_ENOMEM;
+  }
+  OT_CUDA(cudaMemcpyAsync(in.h_ctrl, in.ctrl, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  OT_CUDA(cudaStreamSynchronize(s));
+  const int err = ((int*)in.h_ctrl)[18];
+  if (err & kErrNonFinite) {
+    ctx.set_error("weights must be finite and > 0 (or set zero_mass_floor)");
+    return OT_EINVAL;
+  }
+  in.k = 0;
+  return OT_OK;
+}
+
+void instance_free(Instance& in) {
+  for (auto& kv : in.graphs) cudaGraphExecDestroy(kv.second);
+  in.graphs.clear();
+  for (auto& kv : in.graph_events)
+    for (cudaEvent_t e : kv.second) cudaEventDestroy(e);
+  in.graph_events.clear();
+  if (in.mem) cudaFree(in.mem);
+  if (in.h_ctrl) cudaFreeHost(in.h_ctrl);
+  in.mem = nullptr;
+  in.h_ctrl = nullptr;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Iterations
+// ---------------------------------------------------------------------------------------------
+static cudaError_t issue_iteration(Instance& in, bool cert, cudaEvent_t* ev = nullptr) {
+  const LaunchPlan& pl = cert ? in.cert : in.fast;
+  SweepFn fr = get_sweep(in.d, pl.mode, pl.R, pl.ch, cert ? 4 : 0);
+  SweepFn fc = get_sweep(in.d, pl.mode, pl.R, pl.ch, cert ? 2 : 1);
+  cudaError_t e;
+  if (ev && (e = cudaEventRecordWithFlags(ev[0], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+  e = launch_sweep(fr, in.d_inst, pl.d_row, pl.n_row, pl.grid_row, in.stream);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecordWithFlags(ev[1], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+  e = launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.stream);
+  if (e != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecordWithFlags(ev[2], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+// `count` iterations, the last one a certificate iteration if cert_last; replayed from a CUDA graph.
+// In profiling mode the graph also records an event between consecutive sweeps, and the chunk is
+// waited for so that the per-launch durations can be read.
+static ot_status issue_chunk(Context& ctx, Instance& in, int64_t count, bool cert_last) {
+  if (count <= 0) return OT_OK;
+  const bool prof = ctx.profile;
+  const std::pair<int64_t, int> key(count, (cert_last ? 1 : 0) | (prof ? 2 : 0));
+  auto it = in.graphs.find(key);
+  std::vector<cudaEvent_t>* evs = nullptr;
+  if (prof) {
+    evs = &in.graph_events[key];
+    if (evs->empty()) {
+      evs->resize(2 * count + 1);
+      for (auto& e : *evs) OT_CUDA(cudaEventCreate(&e));
+    }
+  }
+  if (it == in.graphs.end() && in.use_graphs && count <= 4096) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(in.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      cudaError_t e = cudaSuccess;
+      for (int64_t i = 0; i < count && e == cudaSuccess; ++i)
+        e = issue_iteration(in, cert_last && i == count - 1, prof ? evs->data() + 2 * i : nullptr);
+      cudaError_t e2 = cudaStreamEndCapture(in.stream, &g);
+      if (e == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
+        it = in.graphs.emplace(key, ge).first;
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+  }
+  if (it != in.graphs.end()) {
+    OT_CUDA(cudaGraphLaunch(it->second, in.stream));
+  } else {
+    for (int64_t i = 0; i < count; ++i)
+      OT_CUDA(issue_iteration(in, cert_last && i == count - 1, prof ? evs->data() + 2 * i : nullptr));
+  }
+  in.k += count;
+  ctx.launches += 2 * count;
+  if (prof) {
+    OT_CUDA(cudaStreamSynchronize(in.stream));
+    const double entries = (double)in.n * (double)in.m;
+    for (int64_t i = 0; i < count; ++i) {
+      const bool c = cert_last && i == count - 1;
+      float ms_r = 0, ms_c = 0;
+      OT_CUDA(cudaEventElapsedTime(&ms_r, (*evs)[2 * i], (*evs)[2 * i + 1]));
+      OT_CUDA(cudaEventElapsedTime(&ms_c, (*evs)[2 * i + 1], (*evs)[2 * i + 2]));
+      KernelStats& sr = ctx.stats[c ? 2 : 0];
+      KernelStats& sc = ctx.stats[c ? 3 : 1];
+      sr.launches += 1;
+      sr.entries += entries;
+      sr.ms += ms_r;
+      sc.launches += 1;
+      sc.entries += entries;
+      sc.ms += ms_c;
+    }
+  }
+  return OT_OK;
+}
+
+// Read the control block (certificate record, k, error bits) after the stream drains.
+static ot_status read_ctrl(Context& ctx, Instance& in) {
+  OT_CUDA(cudaMemcpyAsync(in.h_ctrl, in.ctrl, 16 * sizeof(double), cudaMemcpyDeviceToHost, in.stream));
+  OT_CUDA(cudaStreamSynchronize(in.stream));
+  const int err = ((int*)in.h_ctrl)[18];
+  in.device_errors |= err;
+  if (err & kErrTimeout) {
+    ctx.set_error("a device wait exceeded its bound");
+    return OT_ETIMEDOUT;
+  }
+  if (err & kErrNonFinite) {
+    ctx.set_error("non-finite potential at iteration %lld", (long long)in.k);
+    return OT_ENUMERIC;
+  }
+  return OT_OK;
+}
+
+// Fold the certificate just read into the best-so-far bounds (App. G.3) and the retained iterate.
+static ot_status absorb_cert(Context& ctx, Instance& in) {
+  const double* c = in.h_ctrl;
+  in.U = c[kCertU];
+  in.L = c[kCertL];
+  in.eps_last = c[kCertEps];
+  in.n_certs += 1;
+  in.last_cert_k = in.k;
+  in.U_best = std::min(in.U_best, in.U);
+  in.L_best = std::max(in.L_best, in.L);
+  const double rel = (in.U - in.L) / std::fabs(in.U);
+  if (in.best_iter < 0 || rel < in.best_rel) {
+    in.best_rel = rel;
+    in.best_iter = in.k - 1;
+    OT_CUDA(cudaMemcpyAsync(in.f_best, in.h.f_cur, in.n * sizeof(double), cudaMemcpyDeviceToDevice, in.stream));
+    OT_CUDA(cudaMemcpyAsync(in.g_best, in.h.g_cur, in.m * sizeof(double), cudaMemcpyDeviceToDevice, in.stream));
+  }
+  return OT_OK;
+}
+
+static void fill_result(const Instance& in, ot_result* r) {
+  if (!r) return;
+  r->iters = in.k;
+  r->best_iter = in.best_iter;
+  r->n_certs = in.n_certs;
+  r->U = in.U;
+  r->L = in.L;
+  r->U_best = in.U_best;
+  r->L_best = in.L_best;
+  r->gap_abs = in.U_best - in.L_best;
+  r->gap_rel = (in.U_best - in.L_best) / std::fabs(in.U_best);
+  r->eps_final = in.k > 0 ? in.h.eta / (in.h.lambda * (double)(in.k - 1) + 1.0) : in.h.eta;
+  r->elapsed_s = in.elapsed_s;
+  r->kappa = in.kappa;
+  r->omega = in.omega;
+  r->stop = in.stop;
+  r->device_errors = in.device_errors;
+}
+
+// Run n iterations; certificate iterations where (k+1) % cert_every == 0, plus the final iteration
+// when final_cert.  Stops early when `stop_rule` and the tolerance is met or time runs out.
+ot_status run_iterations(Context& ctx, Instance& in, int64_t n_iters, bool stop_rule, bool final_cert) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int ce = in.params.cert_every;
+  const int64_t k_end = in.k + n_iters;
+  in.stop = OT_STOP_NONE;
+  while (in.k < k_end) {
+    int64_t chunk = k_end - in.k;
+    if (ce > 0) chunk = std::min<int64_t>(chunk, ce - (in.k % ce));
+    const bool cert = ce > 0 && ((in.k + chunk) % ce == 0 || (final_cert && in.k + chunk == k_end));
+    ot_status st = issue_chunk(ctx, in, chunk, cert);
+    if (st != OT_OK) return st;
+    if (cert || in.k == k_end) {
+      st = read_ctrl(ctx, in);
+      if (st != OT_OK) return st;
+      if (cert) {
+        st = absorb_cert(ctx, in);
+        if (st != OT_OK) return st;
+      }
+    }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    in.elapsed_s = in.elapsed_base + el;
+    if (stop_rule && cert) {
+      const double gap = in.U_best - in.L_best;
+      const double ta = in.params.tol_abs, tr = in.params.tol_rel;
+      if ((ta > 0 && gap <= ta) || (tr > 0 && gap <= tr * std::fabs(in.U_best))) {
+        in.stop = OT_STOP_TOL;
+        break;
+      }
+    }
+    if (stop_rule && in.params.time_budget_s > 0 && el >= in.params.time_budget_s) {
+      in.stop = OT_STOP_TIME;
+      break;
+    }
+  }
+  if (in.stop == OT_STOP_NONE && stop_rule) in.stop = OT_STOP_MAX_ITERS;
+  in.elapsed_base = in.elapsed_s;
+  return OT_OK;
+}
+
+ot_status standalone_certificate(Context& ctx, Instance& in) {
+  const LaunchPlan& pl = in.cert;
+  SweepFn fc = get_sweep(in.d, pl.mode, pl.R, pl.ch, 3);
+  OT_CUDA(launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.stream));
+  ctx.launches += 1;
+  return read_ctrl(ctx, in);
+}
+
+}  // namespace ot
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+using namespace ot;
+
+struct ot_context {
+  Context c;
+};
+struct ot_state {
+  ot_context* ctx;
+  Instance in;
+};
+
+extern "C" {
+
+void ot_params_default(ot_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->eps0 = 1.0;
+  p->lambda = 1.0;
+  p->max_iters = 1000;
+  p->cert_every = 100;
+  p->precision = OT_EXP_MUFU;
+}
+
+const char* ot_status_str(ot_status s) {
+  switch (s) {
+    case OT_OK: return "OT_OK";
+    case OT_EINVAL: return "OT_EINVAL: invalid argument";
+    case OT_ENOMEM: return "OT_ENOMEM: allocation failed";
+    case OT_ECUDA: return "OT_ECUDA: CUDA error";
+    case OT_ENUMERIC: return "OT_ENUMERIC: non-finite value";
+    case OT_ETIMEDOUT: return "OT_ETIMEDOUT: device wait bound exceeded";
+    case OT_EBUSY: return "OT_EBUSY: not finished";
+    case OT_ECANCELLED: return "OT_ECANCELLED: cancelled";
+    case OT_ENOTFOUND: return "OT_ENOTFOUND: unknown request";
+  }
+  return "unknown status";
+}
+
+const char* ot_last_error(const ot_context* ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+ot_status ot_context_create(int device, ot_context** out) {
+  if (!out) return OT_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return OT_EINVAL;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return OT_ECUDA;
+  ot_context* c = new (std::nothrow) ot_context();
+  if (!c) return OT_ENOMEM;
+  c->c.device = device;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->c.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return OT_ECUDA;
+  }
+  c->c.sms = prop.multiProcessorCount;
+  c->c.cc_major = prop.major;
+  c->c.cc_minor = prop.minor;
+  *out = c;
+  return OT_OK;
+}
+
+void ot_context_destroy(ot_context* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->c.device);
+  if (ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
+  delete ctx;
+}
+
+static cudaStream_t pick_stream(ot_context* ctx, const ot_params* p) {
+  return (p && p->stream) ? (cudaStream_t)(uintptr_t)p->stream : ctx->c.stream;
+}
+
+ot_status ot_state_create(ot_context* ctx, const ot_problem* prob, const ot_params* params, ot_state** out) {
+  if (!ctx || !out) return OT_EINVAL;
+  *out = nullptr;
+  cudaSetDevice(ctx->c.device);
+  ot_state* s = new (std::nothrow) ot_state();
+  if (!s) return OT_ENOMEM;
+  s->ctx = ctx;
+  ot_status st = instance_init(ctx->c, s->in, prob, params, pick_stream(ctx, params));
+  if (st != OT_OK) {
+    instance_free(s->in);
+    delete s;
+    return st;
+  }
+  *out = s;
+  return OT_OK;
+}
+
+void ot_state_destroy(ot_state* st) {
+  if (!st) return;
+  cudaSetDevice(st->ctx->c.device);
+  cudaStreamSynchronize(st->in.stream);
+  instance_free(st->in);
+  delete st;
+}
+
+ot_status ot_step(ot_state* st, int64_t n_iters, ot_result* res) {
+  if (!st || n_iters < 0) return OT_EINVAL;
+  cudaSetDevice(st->ctx->c.device);
+  ot_status s = run_iterations(st->ctx->c, st->in, n_iters, false, false);
+  if (s == OT_OK && st->in.k > 0) s = read_ctrl(st->ctx->c, st->in);
+  fill_result(st->in, res);
+  return s;
+}
+
+ot_status ot_certificate(ot_state* st, ot_result* res) {
+  if (!st) return OT_EINVAL;
+  Instance& in = st->in;
+  if (in.k < 1) {
+    st->ctx->c.set_error("no completed iteration to certify");
+    return OT_EINVAL;
+  }
+  cudaSetDevice(st->ctx->c.device);
+  if (in.last_cert_k != in.k) {
+    ot_status s = standalone_certificate(st->ctx->c, in);
+    if (s != OT_OK) return s;
+  } else {
+    ot_status s = read_ctrl(st->ctx->c, in);
+    if (s != OT_OK) return s;
+  }
+  fill_result(in, res);
+  if (res) {
+    res->U = in.h_ctrl[kCertU];
+    res->L = in.h_ctrl[kCertL];
+    res->eps_final = in.h_ctrl[kCertEps];
+  }
+  return OT_OK;
+}
+
+static double* vec_ptr(Instance& in, int which, size_t* len) {
+  Inst& h = in.h;
+  switch (which) {
+    case OT_LOG_ALPHA: *len = in.n; return h.log_alpha;
+    case OT_LOG_ALPHA_HAT: *len = in.n; return h.log_alpha_hat;
+    case OT_LOG_BETA: *len = in.m; return h.log_beta;
+    case OT_LOG_BETA_PREV: *len = in.m; return h.log_beta_prev;
+    case OT_LOG_BETA_HAT: *len = in.m; return h.log_beta_hat;
+    case OT_LOG_BETA_TILDE: *len = in.m; return h.log_beta_tilde;
+    case OT_F_CERT: *len = in.n; return h.f_cur;
+    case OT_G_CERT: *len = in.m; return h.g_cur;
+    case OT_F_BEST: *len = in.n; return in.f_best;
+    case OT_G_BEST: *len = in.m; return in.g_best;
+  }
+  return nullptr;
+}
+
+ot_status ot_state_get(ot_state* st, int which, double* out, int64_t* k) {
+  if (!st) return OT_EINVAL;
+  Context& ctx = st->ctx->c;
+  cudaSetDevice(ctx.device);
+  size_t len = 0;
+  double* p = vec_ptr(st->in, which, &len);
+  if (!p) return OT_EINVAL;
+  if (out) {
+    OT_CUDA(cudaMemcpyAsync(out, p, len * sizeof(double), cudaMemcpyDeviceToHost, st->in.stream));
+    OT_CUDA(cudaStreamSynchronize(st->in.stream));
+  }
+  if (k) *k = st->in.k;
+  return OT_OK;
+}
+
+ot_status ot_state_set(ot_state* st, int which, const double* in_vec, int64_t k) {
+  if (!st || !in_vec || k < 0) return OT_EINVAL;
+  if (which != OT_LOG_ALPHA && which != OT_LOG_BETA && which != OT_LOG_BETA_PREV) return OT_EINVAL;
+  Context& ctx = st->ctx->c;
+  Instance& in = st->in;
+  cudaSetDevice(ctx.device);
+  size_t len = 0;
+  double* p = vec_ptr(in, which, &len);
+  OT_CUDA(cudaMemcpyAsync(p, in_vec, len * sizeof(double), cudaMemcpyHostToDevice, in.stream));
+  const long long kk = k;
+  OT_CUDA(cudaMemcpyAsync(in.h.k, &kk, sizeof(kk), cudaMemcpyHostToDevice, in.stream));
+  OT_CUDA(launch_repack_cols(in.d_inst, (int)in.m, in.stream));
+  ctx.launches += 1;
+  OT_CUDA(cudaStreamSynchronize(in.stream));
+  in.k = k;
+  in.last_cert_k = -1;
+  return OT_OK;
+}
+
+ot_status ot_profile_enable(ot_context* ctx, int on) {
+  if (!ctx) return OT_EINVAL;
+  ctx->c.profile = on != 0;
+  return OT_OK;
+}
+
+ot_status ot_profile_reset(ot_context* ctx) {
+  if (!ctx) return OT_EINVAL;
+  for (auto& s : ctx->c.stats) s = KernelStats();
+  ctx->c.launches = 0;
+  return OT_OK;
+}
+
+ot_status ot_launch_count(ot_context* ctx, int64_t* launches) {
+  if (!ctx || !launches) return OT_EINVAL;
+  *launches = ctx->c.launches;
+  return OT_OK;
+}
+
+ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* entries, double* ms) {
+  if (!ctx || kind < 0 || kind > 3) return OT_EINVAL;
+  const KernelStats& s = ctx->c.stats[kind];
+  if (launches) *launches = s.launches;
+  if (entries) *entries = s.entries;
+  if (ms) *ms = s.ms;
+  return OT_OK;
+}
+
+ot_status ot_state_cost(ot_state* st, double* kappa, double* omega) {
+  if (!st) return OT_EINVAL;
+  if (kappa) *kappa = st->in.kappa;
+  if (omega) *omega = st->in.omega;
+  return OT_OK;
+}
+
+ot_status ot_solve(ot_context* ctx, const ot_problem* prob, const ot_params* params, double* f_out, double* g_out,
+                   ot_result* res) {
+  if (!ctx) return OT_EINVAL;
+  ot_state* st = nullptr;
+  ot_status s = ot_state_create(ctx, prob, params, &st);
+  if (s != OT_OK) return s;
+  Context& c = ctx->c;
+  Instance& in = st->in;
+  s = run_iterations(c, in, params->max_iters, true, true);
+  if (s == OT_OK) {
+    const cudaMemcpyKind kd = prob->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const bool have = in.best_iter >= 0;
+    if (f_out && have &&
+        cudaMemcpyAsync(f_out, in.f_best, in.n * sizeof(double), kd, in.stream) != cudaSuccess)
+      s = OT_ECUDA;
+    if (g_out && have &&
+        cudaMemcpyAsync(g_out, in.g_best, in.m * sizeof(double), kd, in.stream) != cudaSuccess)
+      s = OT_ECUDA;
+    if (cudaStreamSynchronize(in.stream) != cudaSuccess) s = OT_ECUDA;
+  }
+  fill_result(in, res);
+  ot_state_destroy(st);
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Internal host-side types of the solver runtime (not part of the C ABI).
+#pragma once
+#include <cmath>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ot.h"
+#include "ot_kernels.cuh"
+
+namespace ot {
+
+typedef void (*SweepFn)(const Inst*, const Item*, int);
+SweepFn get_sweep(int d, int mode, int R, int ch, int variant);
+
+// Accumulated timing of one kind of sweep launch (profiling mode).
+struct KernelStats {
+  int64_t launches = 0;
+  double entries = 0;  // algorithmic implicit entries (n * m per sweep)
+  double ms = 0;       // summed CUDA-event durations on the launching stream
+};
+
+struct Context {
+  int device = 0;
+  bool profile = false;
+  KernelStats stats[4];  // fast row, fast column, certificate row, certificate column
+  int64_t launches = 0;  // every kernel this context has launched (graph nodes included)
+  int sms = 148;
+  int cc_major = 0, cc_minor = 0;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  std::map<const void*, int> occ;  // resident CTAs per sweep kernel
+  void set_error(const char* fmt, ...);
+  int resident_ctas(SweepFn fn);
+};
+
+// Launch plan of one kind of sweep (fast iterations, or certificate iterations): points per
+// thread, chunk width, split counts, work items and grid of both sweeps.
+struct LaunchPlan {
+  int mode = 0;
+  int R = 1, ch = 16;
+  int pblk_row = 0, pblk_col = 0;
+  int splits_row = 1, splits_col = 1;
+  Item* d_row = nullptr;
+  Item* d_col = nullptr;
+  int n_row = 0, n_col = 0;
+  int grid_row = 0, grid_col = 0;
+};
+
+// One resident instance: descriptor, device buffers, launch plans and host-side bookkeeping.
+struct Instance {
+  Inst h{};                      // host mirror of the device descriptor
+  Inst* d_inst = nullptr;        // device descriptor (inside mem)
+  LaunchPlan fast, cert;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  float* xraw = nullptr;
+  float* yraw = nullptr;
+  double* f_best = nullptr;
+  double* g_best = nullptr;
+  double* ctrl = nullptr;        // device control block: cert record, k, error bits
+  double* h_ctrl = nullptr;      // pinned host copy
+  cudaStream_t stream = nullptr;
+  ot_params params{};
+  int64_t n = 0, m = 0;
+  int d = 0;
+  int sweep_mode = 0, cert_mode = 1, exp_mode = 0;
+  bool use_graphs = true;
+  double kappa = 0, omega = 0;
+  // iteration bookkeeping
+  int64_t k = 0;
+  int64_t last_cert_k = -1;
+  int64_t n_certs = 0;
+  int64_t best_iter = -1;
+  double U = NAN, L = NAN, U_best = INFINITY, L_best = -INFINITY, best_rel = INFINITY, eps_last = NAN;
+  double elapsed_s = 0, elapsed_base = 0;
+  int stop = OT_STOP_NONE;
+  int device_errors = 0;
+  std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
+  std::map<std::pair<int64_t, int>, std::vector<cudaEvent_t>> graph_events;  // profiling mode
+};
+
+ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q);
+void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl);
+ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
+void instance_free(Instance& in);
+ot_status run_iterations(Context& ctx, Instance& in, int64_t n_iters, bool stop_rule, bool final_cert);
+ot_status standalone_certificate(Context& ctx, Instance& in);
+
+}  // namespace ot

@@ -1,0 +1,702 @@
+// Sweep kernels of Dual (O-)BDRS (Algorithm 1, log domain) with the certificate of
+// Proposition 3 / Algorithm 2 fused into the column sweep, for sm_103a.
+//
+// Notation.  A sweep has a "thread side" P (the points whose LSE is computed, R per thread) and a
+// "tile side" Q (the points reduced over, streamed through shared memory by TMA bulk copies).
+// Row sweep: P = sources x_i, Q = targets y_j.  Column sweep: P = targets, Q = sources.
+// With C_pq = kappa ||u_p - w_q||^2 and the tile-side log scaling lv_q (log beta-tilde for the
+// row sweep, log alpha-hat for the column sweep), the exponent of Algorithm 1 in base 2 is
+//
+//     (lv_q - C_pq/eps) log2(e) = z_pq - kappa ||u_p||^2 log2(e) / eps,
+//     z_pq = h_q + <A_p, w_q>,   h_q = (lv_q - kappa ||w_q||^2 / eps) log2(e),
+//                                A_p = (2 kappa log2(e) / eps) u_p,
+//
+// so one entry costs d fused multiply-adds for z, one subtraction of the running shift, one exp2
+// and one addition: the cost matrix is recomputed in registers and never stored.
+//
+// Every (point block, split) work item writes a partial (shift, sum[, cost sum]) per point; the
+// last CTA to finish a point block merges the splits in a fixed order (deterministic) and runs
+// the FP64 epilogue of Algorithm 1 for those points; on the column side the last point block of
+// an instance also advances k and, on certificate iterations, finishes the certificate sums.
+#pragma once
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+
+#include "ot_device.cuh"
+#include "ot_kernels.cuh"
+
+namespace ot {
+
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr float kTau = 32.0f;            // lazy-rescale threshold (base-2 units above the shift)
+constexpr float kPadH = -1.0e30f;        // h of padding points: contributes exp2(-1e30) = 0
+
+// ---------------------------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+__device__ __forceinline__ size_t pack_idx(int p, int comp) {
+  return ((size_t)(p / kTQ) * kNComp + comp) * kTQ + (p % kTQ);
+}
+
+__device__ __forceinline__ void store_h(float* pack, int p, int d, double h) {
+  const float hi = __double2float_rn(h);
+  const float lo = __double2float_rn(h - (double)hi);
+  pack[pack_idx(p, d)] = hi;
+  pack[pack_idx(p, d + 1)] = lo;
+}
+
+// 2^e for an integer-valued e <= 0, exact; 0 below the normal range.
+__device__ __forceinline__ double pow2i(double e) {
+  if (!(e > -1022.0)) return 0.0;
+  return __longlong_as_double((long long)(1023 + (int)e) << 52);
+}
+
+__device__ __forceinline__ double eps_of(const Inst* I, long long k) {
+  return I->eta / (I->lambda * (double)k + 1.0);
+}
+
+// Deterministic CTA-wide sum (fixed tree order); all threads must call it.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int tid = threadIdx.x;
+  red[tid] = v;
+  __syncthreads();
+#pragma unroll
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+template <int MODE>
+struct PartT { typedef float4 type; };
+template <>
+struct PartT<kSweepF64> { typedef double4 type; };
+
+// Partials written by other CTAs are read through L2 (the L1 of this SM is not coherent).
+__device__ __forceinline__ float4 load_part(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ double4 load_part(const double4* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  const double2 a = __ldcg(q), b = __ldcg(q + 1);
+  return make_double4(a.x, a.y, b.x, b.y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-thread accumulator state for R thread-side points.
+// ---------------------------------------------------------------------------------------------
+template <int R, int MODE>
+struct Acc;
+
+template <int R>
+struct Acc<R, kSweepFast> {
+  float mref[R], s[R], kc[R], n[R], nc[R];
+  u64 acc[R], M2[R];
+};
+template <int R>
+struct Acc<R, kSweepComp> {
+  float mref[R], s[R], kc[R], n[R], nc[R];
+};
+template <int R>
+struct Acc<R, kSweepF64> {
+  double mref[R], s[R], n[R];
+};
+
+// ---------------------------------------------------------------------------------------------
+// The sweep kernel.
+//   MODE   kSweepFast: FP32 exponent, f32x2 FMAs, MUFU exp2 (the hot path)
+//          kSweepComp: exponent in float-float (error-free transforms), MUFU exp2, Kahan sums
+//          kSweepF64 : exponent, exp2 and sums in FP64
+//   SIDE   0 = row sweep (Algorithm 1 row update), 1 = column sweep (column update)
+//   CERT   column sweep also accumulates N_q = sum_p ||u-w||^2 E_pq (Algorithm 2)
+//   UPDATE false: standalone certificate of the current state, no state update
+// ---------------------------------------------------------------------------------------------
+template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
+__global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict__ insts,
+                                                         const Item* __restrict__ items, int nitems) {
+  static_assert(!(CERT && MODE == kSweepFast), "certificate sweeps use the compensated or FP64 mode");
+  static_assert(UPDATE || (CERT && SIDE == 1), "a non-updating sweep is the standalone certificate");
+  constexpr bool ACCN = CERT && SIDE == 1;  // accumulate N_q (Algorithm 2) on the column sweep
+  typedef typename PartT<MODE>::type Part;
+  constexpr int NC = (MODE == kSweepFast) ? D + 1 : D + 2;
+  constexpr uint32_t kPackTileBytes = kNComp * kTQ * 4;  // one pack tile, all components
+  constexpr int kStageFloats = kStageTiles * kNComp * kTQ;
+  constexpr int CH = (MODE == kSweepFast) ? CHF : 8;  // columns per chunk (one max + rescale test)
+  static_assert(CH % 4 == 0 && kTQ % CH == 0, "chunk must divide the tile");
+
+  extern __shared__ __align__(128) float smem[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  __shared__ double red[kThreads];
+  __shared__ int s_flag;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  uint32_t gstage = 0;  // pipeline stages consumed by this CTA so far (stage index and parity)
+
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const Item item = items[it];
+    const Inst* __restrict__ I = insts + item.inst;
+    const int np = SIDE == 0 ? I->n : I->m;
+    const int qtiles = SIDE == 0 ? I->tiles_y : I->tiles_x;
+    const int splits = item.nsplit;
+    const int pblks = (np + kThreads * R - 1) / (kThreads * R);
+    const float* __restrict__ ppack = SIDE == 0 ? I->xpack : I->ypack;
+    const float* __restrict__ qpack = SIDE == 0 ? I->ypack : I->xpack;
+    const int tps = (qtiles + splits - 1) / splits;
+    const int qt0 = item.split * tps;
+    const int qt1 = min(qtiles, qt0 + tps);
+    const int ntl = qt1 - qt0;
+    const long long kiter = *I->k - (UPDATE ? 0 : 1);
+    const double eps = eps_of(I, kiter);
+    const double inv_eps = 1.0 / eps;
+    const double sig = 2.0 * I->kappa * kLog2e * inv_eps;
+
+    // ---- thread-side points ----
+    float u[R][D];
+    float Ah[R][D], Al[R][D];
+    double Ad[R][D];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+      const bool valid = p < np;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        u[r][k] = valid ? ppack[pack_idx(p, k)] : 0.0f;
+        const double A = sig * (double)u[r][k];
+        Ad[r][k] = A;
+        Ah[r][k] = __double2float_rn(A);
+        Al[r][k] = __double2float_rn(A - (double)Ah[r][k]);
+      }
+    }
+    Acc<R, MODE> st;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      st.mref[r] = 0;
+      st.s[r] = 0;
+      if constexpr (MODE != kSweepF64) {
+        st.kc[r] = 0.0f;
+        st.n[r] = 0.0f;
+        st.nc[r] = 0.0f;
+      } else {
+        st.n[r] = 0.0;
+      }
+      if constexpr (MODE == kSweepFast) {
+        st.acc[r] = 0ull;
+        st.M2[r] = 0ull;
+      }
+    }
+    u64 A2[R][D];
+    if constexpr (MODE == kSweepFast) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < D; ++k) A2[r][k] = pk2(Ah[r][k], Ah[r][k]);
+    }
+
+    // ---- pipeline prologue: each stage holds up to kStageTiles consecutive pack tiles ----
+    const int nst = (ntl + kStageTiles - 1) / kStageTiles;
+    if (tid == 0) {
+      const int pre = min(nst, kStages);
+      for (int j = 0; j < pre; ++j) {
+        const int stg = (gstage + j) % kStages;
+        const int tiles = min(kStageTiles, ntl - j * kStageTiles);
+        mbar_expect_tx(&bars[stg], tiles * kPackTileBytes);
+        bulk_g2s(smem + stg * kStageFloats, qpack + (size_t)(qt0 + j * kStageTiles) * kNComp * kTQ,
+                 tiles * kPackTileBytes, &bars[stg]);
+      }
+    }
+
+    bool fresh = true;
+    for (int us = 0; us < nst; ++us) {
+      const uint32_t g = gstage + us;
+      const int stg = g % kStages;
+      const uint32_t par = (g / kStages) & 1u;
+      const bool ok = mbar_wait_bounded(&bars[stg], par, kWaitLimit);
+      const int stage_tiles = min(kStageTiles, ntl - us * kStageTiles);
+      for (int tt = 0; tt < stage_tiles; ++tt) {
+      const float* __restrict__ S = smem + stg * kStageFloats + tt * (kNComp * kTQ);
+
+      if constexpr (MODE == kSweepFast) {
+        // Per chunk of CH columns: exponents (f32x2 FMAs), chunk maximum and lazy rescale, then
+        // exp2 on the SFU with a pairwise sum.
+        u64 va[R][CH / 2];
+        auto exponents = [&](u64 (&v)[R][CH / 2], int c0) {
+#pragma unroll
+          for (int gq = 0; gq < CH / 4; ++gq) {
+            const int c = c0 + 4 * gq;
+            const float4 hq = *reinterpret_cast<const float4*>(S + D * kTQ + c);
+            const u64 h01 = pk2(hq.x, hq.y), h23 = pk2(hq.z, hq.w);
+            u64 w01[D], w23[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              const float4 wq = *reinterpret_cast<const float4*>(S + k * kTQ + c);
+              w01[k] = pk2(wq.x, wq.y);
+              w23[k] = pk2(wq.z, wq.w);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              u64 a0 = fma2(A2[r][0], w01[0], h01);
+              u64 a1 = fma2(A2[r][0], w23[0], h23);
+#pragma unroll
+              for (int k = 1; k < D; ++k) {
+                a0 = fma2(A2[r][k], w01[k], a0);
+                a1 = fma2(A2[r][k], w23[k], a1);
+              }
+              v[r][2 * gq] = sub2(a0, st.M2[r]);
+              v[r][2 * gq + 1] = sub2(a1, st.M2[r]);
+            }
+          }
+        };
+        // chunk maximum (max3 tree), one warp vote, rare lazy rescale of shift and sums
+        auto rescale = [&](u64 (&v)[R][CH / 2]) {
+          float cm[R];
+          float amax = -INFINITY;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float t[CH];
+#pragma unroll
+            for (int j = 0; j < CH / 2; ++j) up2(v[r][j], t[2 * j], t[2 * j + 1]);
+#pragma unroll
+            for (int w = 1; w < CH; w *= 3)
+#pragma unroll
+              for (int j = 0; j < CH; j += 3 * w) {
+                if (j + 2 * w < CH) t[j] = max3f(t[j], t[j + w], t[j + 2 * w]);
+                else if (j + w < CH) t[j] = fmaxf(t[j], t[j + w]);
+              }
+            cm[r] = t[0];
+            amax = fmaxf(amax, t[0]);
+          }
+          if (__any_sync(0xffffffffu, fresh || amax > kTau)) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              if (fresh || cm[r] > kTau) {
+                const float sh = floorf(cm[r]);
+                if (!fresh) {
+                  const float f = exp2_neg_int(sh);
+                  st.acc[r] = mul2(st.acc[r], pk2(f, f));
+                  st.s[r] *= f;
+                  st.kc[r] *= f;
+                }
+                st.mref[r] += sh;
+                st.M2[r] = pk2(st.mref[r], st.mref[r]);
+                const u64 s2 = pk2(sh, sh);
+#pragma unroll
+                for (int j = 0; j < CH / 2; ++j) v[r][j] = sub2(v[r][j], s2);
+              }
+            }
+          }
+          fresh = false;
+        };
+        // exp2 and a pairwise (tree) sum of the chunk, then one add into the running pair sum
+        auto accumulate = [&](u64 (&v)[R][CH / 2]) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            u64 e[CH / 2];
+#pragma unroll
+            for (int j = 0; j < CH / 2; ++j) {
+              float lo, hi;
+              up2(v[r][j], lo, hi);
+              e[j] = pk2(ex2_mufu(lo), ex2_mufu(hi));
+            }
+#pragma unroll
+            for (int w = 1; w < CH / 2; w *= 2)
+#pragma unroll
+              for (int j = 0; j + w < CH / 2; j += 2 * w) e[j] = add2(e[j], e[j + w]);
+            st.acc[r] = add2(st.acc[r], e[0]);
+          }
+        };
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTQ; c0 += CH) {
+          exponents(va, c0);
+          rescale(va);
+          accumulate(va);
+        }
+        // fold the tile's pair sums into the compensated running sum
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float lo, hi;
+          up2(st.acc[r], lo, hi);
+          st.acc[r] = 0ull;
+          kahan_add(st.s[r], st.kc[r], lo + hi);
+        }
+      } else {
+        // compensated (float-float) or FP64 exponent
+        typedef typename std::conditional<MODE == kSweepF64, double, float>::type V;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kTQ; c0 += CH) {
+          V v[R][CH];
+#pragma unroll
+          for (int cc = 0; cc < CH; ++cc) {
+            const int c = c0 + cc;
+            float w[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) w[k] = S[k * kTQ + c];
+            const float hh = S[D * kTQ + c], hl = S[(D + 1) * kTQ + c];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              if constexpr (MODE == kSweepF64) {
+                double z = (double)hh + (double)hl;
+#pragma unroll
+                for (int k = 0; k < D; ++k) z = fma(Ad[r][k], (double)w[k], z);
+                v[r][cc] = z - st.mref[r];
+              } else {
+                float sb, e0;
+                two_sum(hh, -st.mref[r], sb, e0);
+                float lo = __fadd_rn(e0, hl);
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                  float pp, pe, s2, e2;
+                  two_prod(Ah[r][k], w[k], pp, pe);
+                  two_sum(sb, pp, s2, e2);
+                  sb = s2;
+                  lo = __fadd_rn(lo, __fadd_rn(e2, pe));
+                  lo = __fmaf_rn(Al[r][k], w[k], lo);
+                }
+                v[r][cc] = __fadd_rn(sb, lo);
+              }
+            }
+          }
+          V cm[R];
+          bool need = fresh;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            V mx = v[r][0];
+#pragma unroll
+            for (int cc = 1; cc < CH; ++cc) mx = mx > v[r][cc] ? mx : v[r][cc];
+            cm[r] = mx;
+            need |= mx > (V)kTau;
+          }
+          if (__any_sync(0xffffffffu, need)) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              if (fresh || cm[r] > (V)kTau) {
+                const V sh = floor(cm[r]);
+                if (!fresh) {
+                  if constexpr (MODE == kSweepF64) {
+                    st.s[r] = ldexp(st.s[r], -(int)fmin(sh, 4000.0));
+                    st.n[r] = ldexp(st.n[r], -(int)fmin(sh, 4000.0));
+                  } else {
+                    const float f = exp2_neg_int(sh);
+                    st.s[r] *= f;
+                    st.kc[r] *= f;
+                    st.n[r] *= f;
+                    st.nc[r] *= f;
+                  }
+                }
+                st.mref[r] += sh;
+#pragma unroll
+                for (int cc = 0; cc < CH; ++cc) v[r][cc] -= sh;
+              }
+            }
+          }
+          fresh = false;
+          V cs[R], cn[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) cs[r] = cn[r] = 0;
+#pragma unroll
+          for (int cc = 0; cc < CH; ++cc) {
+            const int c = c0 + cc;
+            float w[D];
+            if constexpr (ACCN) {
+#pragma unroll
+              for (int k = 0; k < D; ++k) w[k] = S[k * kTQ + c];
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              V E;
+              if constexpr (MODE == kSweepF64) E = exp2(v[r][cc]);
+              else E = ex2_mufu(v[r][cc]);
+              cs[r] += E;
+              if constexpr (ACCN) {
+                V d2 = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                  const V df = (V)u[r][k] - (V)w[k];
+                  d2 = df * df + d2;
+                }
+                cn[r] = d2 * E + cn[r];
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if constexpr (MODE == kSweepF64) {
+              st.s[r] += cs[r];
+              st.n[r] += cn[r];
+            } else {
+              kahan_add(st.s[r], st.kc[r], cs[r]);
+              if constexpr (ACCN) kahan_add(st.n[r], st.nc[r], cn[r]);
+            }
+          }
+        }
+      }
+
+      }  // tiles of the stage
+
+      const int all_ok = __syncthreads_and(ok ? 1 : 0);
+      if (!all_ok) {
+        if (tid == 0) {
+          atomicOr(I->err, kErrTimeout);
+          // let the copies already in flight land before the CTA's shared memory is released
+          for (int j = us + 1; j < min(nst, us + kStages); ++j) {
+            const uint32_t gj = gstage + j;
+            mbar_wait_bounded(&bars[gj % kStages], (gj / kStages) & 1u, kWaitLimit);
+          }
+        }
+        return;
+      }
+      if (tid == 0 && us + kStages < nst) {
+        const int j = us + kStages;
+        const int tiles = min(kStageTiles, ntl - j * kStageTiles);
+        mbar_expect_tx(&bars[stg], tiles * kPackTileBytes);
+        bulk_g2s(smem + stg * kStageFloats, qpack + (size_t)(qt0 + j * kStageTiles) * kNComp * kTQ,
+                 tiles * kPackTileBytes, &bars[stg]);
+      }
+    }
+    gstage += nst;
+
+    // ---- write this split's partials ----
+    Part* part = reinterpret_cast<Part*>(I->part);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+      if (p < np) {
+        Part pr;
+        pr.x = st.mref[r];
+        pr.y = st.s[r];
+        pr.z = st.n[r];
+        pr.w = 0;
+        part[(size_t)item.split * np + p] = pr;
+      }
+    }
+
+    // ---- last CTA of this point block runs the epilogue ----
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_flag = (atomicAdd(&I->cnt[item.pblk], 1u) == (unsigned)(splits - 1));
+    __syncthreads();
+    if (!s_flag) continue;
+    __threadfence();
+
+    const double lam = I->lambda;
+    const double inv_lam = 1.0 / lam;
+    const double inv_eps1 = 1.0 / eps_of(I, kiter + 1);
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+      if (p >= np) continue;
+      // merge the splits in index order: a fixed order keeps the result deterministic
+      double mx = -INFINITY, S = 0.0, N = 0.0;
+      for (int s0 = 0; s0 < splits; s0 += 8) {
+        Part pr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (s0 + u < splits) pr[u] = load_part(&part[(size_t)(s0 + u) * np + p]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (s0 + u >= splits) break;
+          const double ms = (double)pr[u].x;  // integer-valued shifts: rescaling is exact
+          if (ms > mx) {
+            const double f = pow2i(mx - ms);
+            S = S * f + (double)pr[u].y;
+            N = N * f + (double)pr[u].z;
+            mx = ms;
+          } else {
+            const double f = pow2i(ms - mx);
+            S += (double)pr[u].y * f;
+            N += (double)pr[u].z * f;
+          }
+        }
+      }
+      const double lse2 = mx + log2(S);
+      if constexpr (SIDE == 0) {
+        const double lse = lse2 * kLn2 - I->xn2[p] * inv_eps;
+        const double lah = I->log_a[p] - lse;
+        bad |= !isfinite(lah);
+        I->log_alpha_hat[p] = lah;
+        I->log_alpha[p] = (1.0 - lam) * I->log_alpha[p] + lam * lah;
+        store_h(I->xpack, p, I->d, (lah - I->xn2[p] * inv_eps) * kLog2e);
+        if constexpr (CERT) {
+          const double f = eps * lah;
+          I->f_cur[p] = f;
+          acc0 += I->a[p] * f;
+        }
+      } else {
+        const double lse = lse2 * kLn2 - I->yn2[p] * inv_eps;  // d_j of Algorithm 2
+        double lbh;
+        double t;
+        if constexpr (UPDATE) {
+          lbh = I->log_b[p] - lse;
+          bad |= !isfinite(lbh);
+          t = I->log_beta_tilde_next[p];
+          I->log_beta_tilde[p] = t;
+          const double bold = I->log_beta[p];
+          const double bnew = (1.0 - lam) * bold + lam * lbh;
+          I->log_beta_prev[p] = bold;
+          I->log_beta[p] = bnew;
+          I->log_beta_hat[p] = lbh;
+          const double tn = bnew + (bnew - bold) * inv_lam;
+          I->log_beta_tilde_next[p] = tn;
+          store_h(I->ypack, p, I->d, (tn - I->yn2[p] * inv_eps1) * kLog2e);
+        } else {
+          lbh = I->log_beta_hat[p];
+          t = I->log_beta_tilde[p];
+        }
+        if constexpr (CERT) {
+          const double sj = exp(t + lse);
+          const double mu = I->kappa * N / S;
+          const double gj = eps * (lbh - I->log_b[p]);
+          I->g_cur[p] = gj;
+          acc0 += I->b[p] * gj;
+          acc1 += sj * mu;
+          acc2 += fabs(sj - I->b[p]);
+        }
+      }
+    }
+    if (bad) atomicOr(I->err, kErrNonFinite);
+    if constexpr (CERT) {
+      const double s0 = block_sum(acc0, red);
+      if constexpr (SIDE == 0) {
+        if (tid == 0) I->blk[item.pblk] = s0;
+      } else {
+        const double s1 = block_sum(acc1, red);
+        const double s2 = block_sum(acc2, red);
+        if (tid == 0) {
+          double* bb = I->blk + I->pblk_x + 3 * item.pblk;
+          bb[0] = s0;
+          bb[1] = s1;
+          bb[2] = s2;
+        }
+      }
+    }
+    if (tid == 0) I->cnt[item.pblk] = 0u;
+
+    if constexpr (SIDE == 1) {
+      // ---- last point block of the instance: advance k, finish the certificate ----
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) s_flag = (atomicAdd(I->done, 1u) == (unsigned)(pblks - 1));
+      __syncthreads();
+      if (!s_flag) continue;
+      __threadfence();
+      if constexpr (CERT) {
+        double rf;
+        if constexpr (UPDATE) {
+          double v = 0.0;
+          for (int b = tid; b < I->pblk_x; b += kThreads) v += __ldcg(&I->blk[b]);
+          rf = block_sum(v, red);
+        } else {
+          // standalone certificate: <r, f> with f = eps log alpha-hat from the state
+          double v = 0.0;
+          for (int i = tid; i < I->n; i += kThreads) {
+            const double f = eps * I->log_alpha_hat[i];
+            I->f_cur[i] = f;
+            v += I->a[i] * f;
+          }
+          rf = block_sum(v, red);
+        }
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+        for (int b = tid; b < pblks; b += kThreads) {
+          const double* bb = I->blk + I->pblk_x + 3 * b;
+          v0 += __ldcg(&bb[0]);
+          v1 += __ldcg(&bb[1]);
+          v2 += __ldcg(&bb[2]);
+        }
+        const double cg = block_sum(v0, red);
+        const double smu = block_sum(v1, red);
+        const double dab = block_sum(v2, red);
+        if (tid == 0) {
+          const double delta = 0.5 * dab;
+          double* cr = I->cert;
+          cr[kCertIter] = (double)kiter;
+          cr[kCertEps] = eps;
+          cr[kCertU] = smu + I->omega * delta;
+          cr[kCertL] = rf + cg;
+          cr[kCertDelta] = delta;
+          cr[kCertCostZ] = smu;
+          cr[kCertRF] = rf;
+          cr[kCertCG] = cg;
+        }
+      }
+      if (tid == 0) {
+        if constexpr (UPDATE) *I->k = kiter + 1;
+        *I->done = 0u;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launch table: one entry per instantiated (D, R, MODE, SIDE, CERT, UPDATE).
+// ---------------------------------------------------------------------------------------------
+typedef void (*SweepFn)(const Inst*, const Item*, int);
+
+template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
+static SweepFn sweep_ptr() {
+  return &sweep_kernel<D, R, MODE, SIDE, CERT, UPDATE, CHF>;
+}
+
+// variant index: 0 row, 1 col, 2 col + certificate, 3 standalone certificate, 4 row + certificate
+template <int D, int R, int MODE, int CHF>
+static SweepFn sweep_variant(int v) {
+  switch (v) {
+    case 0: return sweep_ptr<D, R, MODE, 0, false, true, CHF>();
+    case 1: return sweep_ptr<D, R, MODE, 1, false, true, CHF>();
+    case 2:
+      if constexpr (MODE != kSweepFast) return sweep_ptr<D, R, MODE, 1, true, true, CHF>();
+      return nullptr;
+    case 3:
+      if constexpr (MODE != kSweepFast) return sweep_ptr<D, R, MODE, 1, true, false, CHF>();
+      return nullptr;
+    case 4:
+      if constexpr (MODE != kSweepFast) return sweep_ptr<D, R, MODE, 0, true, true, CHF>();
+      return nullptr;
+  }
+  return nullptr;
+}
+
+// Tile plans of the fast sweep: points per thread R in {1, 2, 4, 8} and chunk width CH in {8, 16}
+// (R = 8 only with CH = 8).  The compensated and FP64 sweeps use CH = 8 and R in {1, 2, 4}.
+template <int D>
+static SweepFn sweep_m(int mode, int R, int ch, int v) {
+  if (mode == kSweepFast) {
+    if (R == 1) return ch == 8 ? sweep_variant<D, 1, kSweepFast, 8>(v) : sweep_variant<D, 1, kSweepFast, 16>(v);
+    if (R == 2) return ch == 8 ? sweep_variant<D, 2, kSweepFast, 8>(v) : sweep_variant<D, 2, kSweepFast, 16>(v);
+    if (R == 4) return ch == 8 ? sweep_variant<D, 4, kSweepFast, 8>(v) : sweep_variant<D, 4, kSweepFast, 16>(v);
+    if (R == 8 && ch == 8) return sweep_variant<D, 8, kSweepFast, 8>(v);
+    return nullptr;
+  }
+  if (mode == kSweepComp) {
+    if (R == 1) return sweep_variant<D, 1, kSweepComp, 8>(v);
+    if (R == 2) return sweep_variant<D, 2, kSweepComp, 8>(v);
+    if (R == 4) return sweep_variant<D, 4, kSweepComp, 8>(v);
+    return nullptr;
+  }
+  if (mode == kSweepF64) {
+    if (R == 1) return sweep_variant<D, 1, kSweepF64, 8>(v);
+    if (R == 2) return sweep_variant<D, 2, kSweepF64, 8>(v);
+    return nullptr;
+  }
+  return nullptr;
+}
+
+}  // namespace ot
