@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--engine", default="serial", choices=["serial"])
+    ap.add_argument("--engine", default="batched", choices=["batched", "serial"])
+    ap.add_argument("--slots", type=int, default=256, help="server slots (batched engine)")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--rate", type=float, default=32.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--max-iters", type=int, default=2000)
@@ -143,6 +144,35 @@ def run_serial(ctx, reqs, probs, dev_inputs, args, host: bool):
         te = time.perf_counter()
         lat.append(te - t0 - r.arrival_s)
         ttg.append(te - ts)
+        entries += 2.0 * p.n * p.m * res["iters"]
+        conv += res["stop"] == "tol"
+    return dict(latency=lat, ttg=ttg, entries=entries, converged=conv, h2d=h2d, d2h=d2h)
+
+
+def run_batched(srv, reqs, probs, dev_inputs, args, host: bool):
+    """Continuous batching: requests are submitted at their arrival times to the server, which
+    admits them at certificate boundaries and batches all running solves in each launch."""
+    t0 = time.perf_counter()
+    ids = []
+    h2d = d2h = 0
+    for r, p, dv in zip(reqs, probs, dev_inputs):
+        now = time.perf_counter() - t0
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        if host:
+            ids.append(srv.submit(p.x, p.y, p.a, p.b, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15,
+                                  **solve_params(args)))
+            h2d += p.x.nbytes + p.y.nbytes + p.a.nbytes + p.b.nbytes
+        else:
+            x, y, a, b = dv
+            ids.append(srv.submit(x, y, a, b, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15,
+                                  **solve_params(args)))
+    lat, ttg, entries, conv = [], [], 0.0, 0
+    for rid, p in zip(ids, probs):
+        f, g, res = srv.wait(rid, -1.0)
+        d2h += f.nbytes + g.nbytes
+        lat.append(res["latency_s"])
+        ttg.append(res["latency_s"] - res["queue_s"])
         entries += 2.0 * p.n * p.m * res["iters"]
         conv += res["stop"] == "tol"
     return dict(latency=lat, ttg=ttg, entries=entries, converged=conv, h2d=h2d, d2h=d2h)
@@ -253,43 +283,62 @@ def run_ours(args, rank: int, world: int):
         if dist:
             td.barrier()
 
+    stream = torch.cuda.Stream()
+    srv = None
+    if args.engine == "batched":
+        srv = P.Server(ctx, hbm_budget_bytes=64 << 30, max_slots=args.slots, stream=stream.cuda_stream)
+
+        def engine(host):
+            return run_batched(srv, reqs, probs, dev_inputs, args, host)
+    else:
+        def engine(host):
+            return run_serial(ctx, reqs, probs, dev_inputs, args, host)
+
     for _ in range(args.warmup):
-        run_serial(ctx, reqs, probs, dev_inputs, args, host=False)
+        engine(False)
         flush_l2(l2buf)
     barrier()
     clock = ClockSampler(dev)
     clock.start()
     lib.ot_profile_reset(ctx.handle)
     lib.ot_profile_enable(ctx.handle, 1)
+    if srv is not None:
+        srv.reset_stats()
+        srv.profile(True)
     step_times, results = [], []
     for _ in range(args.steps):
         flush_l2(l2buf)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        res = run_serial(ctx, reqs, probs, dev_inputs, args, host=False)
-        ev1.record()
+        ev0.record(stream)
+        res = engine(False)
+        ev1.record(stream)
         barrier()
         step_times.append(ev0.elapsed_time(ev1) / 1e3)
         results.append(res)
     lib.ot_profile_enable(ctx.handle, 0)
     clocks = clock.stop()
-    nl = ctypes.c_int64()
-    lib.ot_launch_count(ctx.handle, ctypes.byref(nl))
     kst = []
-    for kind in range(4):
-        n = ctypes.c_int64()
-        e = ctypes.c_double()
-        ms = ctypes.c_double()
-        lib.ot_profile_read(ctx.handle, kind, ctypes.byref(n), ctypes.byref(e), ctypes.byref(ms))
-        kst.append((n.value, e.value, ms.value))
+    if srv is not None:
+        srv.profile(False)
+        nl = ctypes.c_int64(srv.stats()["launches"])
+        kst = [srv.kernel_stats(kind) for kind in range(4)]
+    else:
+        nl = ctypes.c_int64()
+        lib.ot_launch_count(ctx.handle, ctypes.byref(nl))
+        for kind in range(4):
+            n = ctypes.c_int64()
+            e = ctypes.c_double()
+            ms = ctypes.c_double()
+            lib.ot_profile_read(ctx.handle, kind, ctypes.byref(n), ctypes.byref(e), ctypes.byref(ms))
+            kst.append((n.value, e.value, ms.value))
     # end to end: host buffers through the C ABI, copies inside the timed region
     e2e_times, e2e_res = [], []
     for _ in range(args.steps):
         flush_l2(l2buf)
         barrier()
         t = time.perf_counter()
-        r2 = run_serial(ctx, reqs, probs, dev_inputs, args, host=True)
+        r2 = engine(True)
         barrier()
         e2e_times.append(time.perf_counter() - t)
         e2e_res.append(r2)
@@ -310,6 +359,8 @@ def run_ours(args, rank: int, world: int):
         e2e_t = statistics.median(e2e_times)
         e2e_entries = e2e_res[-1]["entries"]
     if rank != 0:
+        if srv is not None:
+            srv.close()
         if dist:
             td.barrier()
         return
@@ -344,6 +395,8 @@ def run_ours(args, rank: int, world: int):
         "clocks": clocks,
     }
     print(json.dumps(out), flush=True)
+    if srv is not None:
+        srv.close()
     if dist:
         td.barrier()
 

@@ -126,6 +126,8 @@ typedef struct {
   double omega;
   int32_t stop;           /* ot_stop_reason */
   int32_t device_errors;  /* raw device error bits (0 when OT_OK) */
+  double latency_s;       /* serving only: submission to completion (0 otherwise) */
+  double queue_s;         /* serving only: submission to admission (0 otherwise) */
 } ot_result;
 
 /* Sensible defaults: eps0 = 1, lambda = 1, max_iters = 1000, cert_every = 100, OT_EXP_MUFU. */
@@ -173,6 +175,52 @@ ot_status ot_state_set(ot_state* st, int which, const double* in, int64_t k);
 
 /* The (kappa, omega) the state uses, after any device-side cost-range pass. */
 ot_status ot_state_cost(ot_state* st, double* kappa, double* omega);
+
+/* ---------------------------------------------------------------------------------------------
+ * Continuous-batching server.  Not in the paper: a serving front end for many independent solves
+ * on one GPU.  ot_serve_submit copies the problem (host arrays, or device arrays when
+ * on_device = 1) and queues it; a scheduler thread admits queued requests in arrival order into
+ * free slots (max_slots) while the summed device memory of the admitted instances stays within
+ * hbm_budget_bytes, and runs all admitted solves of the same d, precision and cert_every as one
+ * batch: each chunk of cert_every iterations is issued as sweep launches whose work items cover
+ * every instance of the batch, the last iteration of the chunk being a certificate iteration
+ * for all of them.  Requests join and leave only at chunk boundaries; each stops by its own rule
+ * (tol_rel / tol_abs on the best certified gap, max_iters rounded up to a multiple of
+ * cert_every, time_budget_s since admission) or cancellation.  cert_every must be >= 1.
+ * All ot_serve_* functions are thread-safe.  Results are the certificate potentials of the
+ * retained iterate (as ot_solve), copied to host buffers f_out (n) and g_out (m), either may be
+ * NULL; a finished request is released by the poll or wait call that returns it.
+ * stream: a cudaStream_t for all of the server's device work (0 = a stream of its own).
+ * --------------------------------------------------------------------------------------------- */
+typedef struct ot_server ot_server;
+
+typedef struct {
+  int64_t submitted, completed, cancelled, failed, active, pending, chunks, launches;
+  double p50_latency_s, p99_latency_s, mean_latency_s;  /* submission to completion, completed requests */
+  double solves_per_s, entries_per_s, entries;          /* since creation or the last reset */
+  double elapsed_s;
+  double hbm_used_bytes;
+} ot_serve_statistics;
+
+ot_status ot_serve_create(ot_context* ctx, size_t hbm_budget_bytes, int32_t max_slots, uint64_t stream,
+                          ot_server** out);
+/* OT_ENOMEM if the request alone exceeds the budget; OT_EINVAL for invalid problems/params. */
+ot_status ot_serve_submit(ot_server* sv, const ot_problem* prob, const ot_params* params, uint64_t* req_id);
+/* OT_EBUSY while queued or running; otherwise the request's own status (OT_OK, OT_ECANCELLED, ...). */
+ot_status ot_serve_poll(ot_server* sv, uint64_t req_id, double* f_out, double* g_out, ot_result* res);
+/* Block until the request finishes or timeout_s passes (OT_EBUSY); timeout_s < 0 waits forever. */
+ot_status ot_serve_wait(ot_server* sv, uint64_t req_id, double timeout_s, double* f_out, double* g_out,
+                        ot_result* res);
+ot_status ot_serve_cancel(ot_server* sv, uint64_t req_id);
+ot_status ot_serve_stats(ot_server* sv, ot_serve_statistics* out);
+/* Zero the statistics, kernel timings and launch count. */
+ot_status ot_serve_reset_stats(ot_server* sv);
+/* Kernel timing of the server's batched sweeps (as ot_profile_enable / ot_profile_read: kinds
+ * 0 fast row, 1 fast column, 2 certificate row, 3 certificate column; entries = sum of n * m over
+ * the instances a launch covers). */
+ot_status ot_serve_profile_enable(ot_server* sv, int on);
+ot_status ot_serve_profile_read(ot_server* sv, int kind, int64_t* launches, double* entries, double* ms);
+void ot_serve_destroy(ot_server* sv);
 
 /* Measurement support (not part of the method): kernel timing.  While enabled on a context, every
  * iteration chunk of its states records a CUDA event on the launching stream before and after each

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libot.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
-        f"{LIB_PATH} is missing: build it with `python -m paper_2609_33814_b300.build` "
+        f"{LIB_PATH} is missing: build it with `python paper_2609_33814_b300/build.py` "
         "(the solver has no CPU fallback)")
 
 _lib = C.CDLL(LIB_PATH)
@@ -56,12 +56,24 @@ class OtResult(C.Structure):
                 ("U", C.c_double), ("L", C.c_double), ("U_best", C.c_double), ("L_best", C.c_double),
                 ("gap_abs", C.c_double), ("gap_rel", C.c_double), ("eps_final", C.c_double),
                 ("elapsed_s", C.c_double), ("kappa", C.c_double), ("omega", C.c_double),
-                ("stop", C.c_int32), ("device_errors", C.c_int32)]
+                ("stop", C.c_int32), ("device_errors", C.c_int32), ("latency_s", C.c_double),
+                ("queue_s", C.c_double)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["stop"] = STOP_NAMES.get(self.stop, self.stop)
         return d
+
+
+class OtServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("cancelled", C.c_int64),
+                ("failed", C.c_int64), ("active", C.c_int64), ("pending", C.c_int64), ("chunks", C.c_int64),
+                ("launches", C.c_int64), ("p50_latency_s", C.c_double), ("p99_latency_s", C.c_double),
+                ("mean_latency_s", C.c_double), ("solves_per_s", C.c_double), ("entries_per_s", C.c_double),
+                ("entries", C.c_double), ("elapsed_s", C.c_double), ("hbm_used_bytes", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _P = C.c_void_p
@@ -80,6 +92,22 @@ _lib.ot_certificate.argtypes = [_P, C.POINTER(OtResult)]
 _lib.ot_state_get.argtypes = [_P, C.c_int, _P, C.POINTER(C.c_int64)]
 _lib.ot_state_set.argtypes = [_P, C.c_int, _P, C.c_int64]
 _lib.ot_state_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.ot_serve_create.argtypes = [_P, C.c_size_t, C.c_int32, C.c_uint64, C.POINTER(_P)]
+_lib.ot_serve_submit.argtypes = [_P, C.POINTER(OtProblem), C.POINTER(OtParams), C.POINTER(C.c_uint64)]
+_lib.ot_serve_poll.argtypes = [_P, C.c_uint64, _P, _P, C.POINTER(OtResult)]
+_lib.ot_serve_wait.argtypes = [_P, C.c_uint64, C.c_double, _P, _P, C.POINTER(OtResult)]
+_lib.ot_serve_cancel.argtypes = [_P, C.c_uint64]
+_lib.ot_serve_stats.argtypes = [_P, C.POINTER(OtServeStats)]
+_lib.ot_serve_reset_stats.argtypes = [_P]
+_lib.ot_serve_destroy.argtypes = [_P]
+_lib.ot_serve_profile_enable.argtypes = [_P, C.c_int]
+_lib.ot_serve_profile_read.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]
+_lib.ot_profile_enable.argtypes = [_P, C.c_int]
+_lib.ot_profile_reset.argtypes = [_P]
+_lib.ot_profile_read.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.ot_launch_count.argtypes = [_P, C.POINTER(C.c_int64)]
+_lib.ot_probe_pipes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int]
 
 
 class OTError(RuntimeError):
@@ -253,3 +281,79 @@ class State:
         kap, om = C.c_double(), C.c_double()
         self.ctx.check(_lib.ot_state_cost(self._h, C.byref(kap), C.byref(om)), "ot_state_cost")
         return kap.value, om.value
+
+
+class Server:
+    """Continuous-batching server (``ot_serve_*``); thread-safe.  Results come back on the host."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int = 8 << 30, max_slots: int = 64, stream: int = 0):
+        self.ctx = ctx
+        h = _P()
+        st = _lib.ot_serve_create(ctx.handle, int(hbm_budget_bytes), int(max_slots), int(stream), C.byref(h))
+        if st != OT_OK:
+            raise OTError(st, "ot_serve_create")
+        self._h = h
+        self._sizes = {}
+
+    def submit(self, x, y, a, b, cost_scale=0.0, omega=0.0, zero_mass_floor=0.0, **params) -> int:
+        prob, keep = make_problem(x, y, a, b, cost_scale, omega, zero_mass_floor)
+        prm = make_params(**params)
+        rid = C.c_uint64()
+        st = _lib.ot_serve_submit(self._h, C.byref(prob), C.byref(prm), C.byref(rid))
+        if st != OT_OK:
+            raise OTError(st, "ot_serve_submit")
+        self._sizes[rid.value] = (int(prob.n), int(prob.m))
+        return int(rid.value)
+
+    def _collect(self, fn, rid, *extra):
+        n, m = self._sizes[rid]
+        f = np.empty(n, np.float64)
+        g = np.empty(m, np.float64)
+        res = OtResult()
+        st = fn(self._h, C.c_uint64(rid), *extra, f.ctypes.data, g.ctypes.data, C.byref(res))
+        if st == OT_EBUSY:
+            return None
+        self._sizes.pop(rid, None)
+        if st != OT_OK:
+            raise OTError(st, f"request {rid}")
+        return f, g, res.as_dict()
+
+    def poll(self, rid: int):
+        """(f, g, result) when finished, None while queued or running."""
+        return self._collect(_lib.ot_serve_poll, rid)
+
+    def wait(self, rid: int, timeout_s: float = -1.0):
+        return self._collect(_lib.ot_serve_wait, rid, C.c_double(timeout_s))
+
+    def cancel(self, rid: int):
+        st = _lib.ot_serve_cancel(self._h, C.c_uint64(rid))
+        if st != OT_OK:
+            raise OTError(st, f"cancel {rid}")
+
+    def stats(self) -> dict:
+        s = OtServeStats()
+        _lib.ot_serve_stats(self._h, C.byref(s))
+        return s.as_dict()
+
+    def reset_stats(self):
+        _lib.ot_serve_reset_stats(self._h)
+
+    def profile(self, on: bool):
+        _lib.ot_serve_profile_enable(self._h, 1 if on else 0)
+
+    def kernel_stats(self, kind: int):
+        """(launches, entries, ms) of one kind of batched sweep since the last reset."""
+        n, e, ms = C.c_int64(), C.c_double(), C.c_double()
+        _lib.ot_serve_profile_read(self._h, int(kind), C.byref(n), C.byref(e), C.byref(ms))
+        return n.value, e.value, ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ot_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

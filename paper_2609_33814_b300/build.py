@@ -1,6 +1,7 @@
 """Build the solver's shared library (libot.so) in-tree for sm_103a with nvcc.
 
-Usage: ``python -m paper_2609_33814_b300.build`` (or ``build()`` from Python).  Each
+Usage: ``python paper_2609_33814_b300/build.py`` (or ``build()`` after loading this file by path;
+importing it through the package would load the library first).  Each
 translation unit under ``csrc/`` is compiled in parallel to an object file under
 ``_build/``, then linked into ``paper_2609_33814_b300/libot.so``.  Objects are rebuilt
 only when a source or header is newer.

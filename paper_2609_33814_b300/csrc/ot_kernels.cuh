@@ -54,13 +54,18 @@ struct Inst {
   double* log_beta_tilde_next;   // beta-tilde^{k} for the next iteration (packed into ypack)
   double* f_cur;                 // certificate potentials of the latest certificate iteration
   double* g_cur;
-  void* part;                    // split partials (float4 or double4 per point and split)
+  void* part;                    // split partials (float4, or PartF64 in FP64 sweeps, per point and split)
   unsigned* cnt;                 // per point-block arrival counters (sized for R = 1)
   unsigned* done;                // per-instance epilogue counter
   double* blk;                   // certificate partial sums: pblk_x row blocks, then 3 per column block
   long long* k;                  // completed iterations
   double* cert;                  // certificate record (kCertLen doubles)
   int* err;                      // error bits
+};
+
+// Split partial of the FP64 sweep: (shift, sum, cost-weighted sum, unused).
+struct alignas(32) PartF64 {
+  double x, y, z, w;
 };
 
 // A unit of sweep work: instance, point block, split of the other side, and the split count of

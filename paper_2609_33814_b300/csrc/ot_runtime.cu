@@ -70,6 +70,7 @@ static int env_int(const char* name, int dflt) {
 void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl) {
   const int np = (int)std::max(in.n, in.m);
   int R, ch = 8;
+  const bool is_fast_plan = &pl == &in.fast;
   if (mode == kSweepF64) {
     R = np >= ctx.sms * kThreads * 4 ? 2 : 1;
   } else if (mode == kSweepComp) {
@@ -81,6 +82,11 @@ void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl) {
     R = env_int("OT_FORCE_R", R);
     ch = env_int("OT_FORCE_CH", ch);
   }
+  if (is_fast_plan && in.force_fast_R > 0) {
+    R = in.force_fast_R;
+    ch = in.force_fast_ch > 0 ? in.force_fast_ch : ch;
+  }
+  if (!is_fast_plan && in.force_cert_R > 0) R = in.force_cert_R;
   if (!get_sweep(in.d, mode, R, ch, 0)) {
     R = 1;
     ch = 16;
@@ -172,15 +178,16 @@ ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q) {
     ctx.set_error("max_iters and cert_every must be >= 0");
     return OT_EINVAL;
   }
-  if (q->precision != OT_EXP_MUFU && q->precision != OT_FP64 && q->precision != OT_FP32_COMP &&
-      q->precision != OT_EXP_POLY && q->precision != OT_EXP_SPLIT) {
-    ctx.set_error("unknown precision %d", q->precision);
+  if (q->precision != OT_EXP_MUFU && q->precision != OT_FP64 && q->precision != OT_FP32_COMP) {
+    ctx.set_error("precision %d is not available", q->precision);
     return OT_EINVAL;
   }
   return OT_OK;
 }
 
-ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream) {
+// Validate, plan and lay out the device buffers of an instance (no allocation): in.bytes is the
+// device memory the instance will hold.
+ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream) {
   ot_status vs = validate(ctx, p, q);
   if (vs != OT_OK) return vs;
   in.n = p->n;
@@ -207,31 +214,55 @@ ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const o
   size_t nsp = 0;
   for (const LaunchPlan* pl : {&in.fast, &in.cert})
     nsp = std::max(nsp, std::max((size_t)pl->splits_row * n, (size_t)pl->splits_col * m));
+  if (in.max_part_splits > 0)
+    nsp = std::max(nsp, std::max((size_t)std::min(in.max_part_splits, h.tiles_y) * n,
+                                 (size_t)std::min(in.max_part_splits, h.tiles_x) * m));
   const size_t maxblk = (std::max(n, m) + kThreads - 1) / kThreads;
+  Layout& L = in.layout;
   Carve cv;
-  const size_t o_xpack = cv.take<float>((size_t)h.tiles_x * kNComp * kTQ);
-  const size_t o_ypack = cv.take<float>((size_t)h.tiles_y * kNComp * kTQ);
-  const size_t o_xraw = cv.take<float>(n * in.d);
-  const size_t o_yraw = cv.take<float>(m * in.d);
-  const size_t o_a = cv.take<double>(n), o_b = cv.take<double>(m);
-  const size_t o_ain = cv.take<double>(n), o_bin = cv.take<double>(m);
-  const size_t o_la = cv.take<double>(n), o_lb = cv.take<double>(m);
-  const size_t o_xn2 = cv.take<double>(n), o_yn2 = cv.take<double>(m);
-  const size_t o_state0 = cv.take<double>(2 * n + 5 * m);  // alpha, alpha_hat, beta, beta_prev, beta_hat, tilde, tilde_next
-  const size_t o_fg = cv.take<double>(2 * (n + m));         // f_cur, g_cur, f_best, g_best
-  const size_t o_part = cv.take<double4>(nsp);
-  const size_t o_cnt = cv.take<unsigned>(maxblk + 1);
-  const size_t o_blk = cv.take<double>((n + kThreads - 1) / kThreads + 3 * ((m + kThreads - 1) / kThreads));
-  const size_t o_ctrl = cv.take<double>(16);
-  const size_t o_range = cv.take<unsigned>(2);
-  const size_t o_inst = cv.take<Inst>(1);
+  L.xpack = cv.take<float>((size_t)h.tiles_x * kNComp * kTQ);
+  L.ypack = cv.take<float>((size_t)h.tiles_y * kNComp * kTQ);
+  L.xraw = cv.take<float>(n * in.d);
+  L.yraw = cv.take<float>(m * in.d);
+  L.a = cv.take<double>(n);
+  L.b = cv.take<double>(m);
+  L.ain = cv.take<double>(n);
+  L.bin = cv.take<double>(m);
+  L.la = cv.take<double>(n);
+  L.lb = cv.take<double>(m);
+  L.xn2 = cv.take<double>(n);
+  L.yn2 = cv.take<double>(m);
+  L.state0 = cv.take<double>(2 * n + 5 * m);  // alpha, alpha_hat, beta, beta_prev, beta_hat, tilde, tilde_next
+  L.fg = cv.take<double>(2 * (n + m));         // f_cur, g_cur, f_best, g_best
+  L.part = cv.take<PartF64>(nsp);
+  L.cnt = cv.take<unsigned>(maxblk + 1);
+  L.maxblk = maxblk;
+  L.blk = cv.take<double>((n + kThreads - 1) / kThreads + 3 * ((m + kThreads - 1) / kThreads));
+  L.ctrl = cv.take<double>(16);
+  L.range = cv.take<unsigned>(2);
+  L.inst = cv.take<Inst>(1);
   const size_t n_items = (size_t)in.fast.n_row + in.fast.n_col + in.cert.n_row + in.cert.n_col;
-  const size_t o_items = cv.take<Item>(n_items);
+  L.items = cv.take<Item>(n_items);
   in.bytes = cv.off;
-  if (cudaMalloc(&in.mem, in.bytes) != cudaSuccess) {
+  return OT_OK;
+}
+
+// Allocate, upload and initialise a prepared instance (Algorithm 1 initialisation).
+ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
+  Inst& h = in.h;
+  const size_t n = in.n, m = in.m;
+  const Layout& L = in.layout;
+  const size_t maxblk = L.maxblk;
+  const size_t o_xpack = L.xpack, o_ypack = L.ypack, o_xraw = L.xraw, o_yraw = L.yraw, o_a = L.a, o_b = L.b,
+               o_ain = L.ain, o_bin = L.bin, o_la = L.la, o_lb = L.lb, o_xn2 = L.xn2, o_yn2 = L.yn2,
+               o_state0 = L.state0, o_fg = L.fg, o_part = L.part, o_cnt = L.cnt, o_blk = L.blk, o_ctrl = L.ctrl,
+               o_range = L.range, o_inst = L.inst, o_items = L.items;
+  (void)o_blk;
+  cudaError_t ae = in.async_alloc ? cudaMallocAsync(&in.mem, in.bytes, in.stream) : cudaMalloc(&in.mem, in.bytes);
+  if (ae != cudaSuccess) {
     cudaGetLastError();
     in.mem = nullptr;
-    ctx.set_error("cudaMalloc of %zu bytes failed", in.bytes);
+    ctx.set_error("device allocation of %zu bytes failed", in.bytes);
     return OT_ENOMEM;
   }
   char* base = (char*)in.mem;
@@ -277,7 +308,7 @@ ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const o
   in.cert.d_row = in.fast.d_col + in.fast.n_col;
   in.cert.d_col = in.cert.d_row + in.cert.n_row;
 
-  cudaStream_t s = stream;
+  cudaStream_t s = in.stream;
   OT_CUDA(cudaMemsetAsync(in.mem, 0, in.bytes, s));
   const cudaMemcpyKind k_in = p->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   OT_CUDA(cudaMemcpyAsync(in.xraw, p->x, n * in.d * sizeof(float), k_in, s));
@@ -328,7 +359,9 @@ ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const o
   OT_CUDA(cudaMemcpyAsync(in.d_inst, &h, sizeof(Inst), cudaMemcpyHostToDevice, s));
   OT_CUDA(launch_repack_cols(in.d_inst, (int)m, s));
   ctx.launches += 1;
-  if (cudaMallocHost(&in.h_ctrl, 16 * sizeof(double)) != cudaSuccess) {
+  if (in.h_ctrl_external) {
+    in.h_ctrl = in.h_ctrl_external;
+  } else if (cudaMallocHost(&in.h_ctrl, 16 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     in.h_ctrl = nullptr;
     ctx.set_error("cudaMallocHost failed");
@@ -345,14 +378,25 @@ ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const o
   return OT_OK;
 }
 
+ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream) {
+  ot_status st = instance_prepare(ctx, in, p, q, stream);
+  if (st != OT_OK) return st;
+  return instance_setup(ctx, in, p);
+}
+
 void instance_free(Instance& in) {
   for (auto& kv : in.graphs) cudaGraphExecDestroy(kv.second);
   in.graphs.clear();
   for (auto& kv : in.graph_events)
     for (cudaEvent_t e : kv.second) cudaEventDestroy(e);
   in.graph_events.clear();
-  if (in.mem) cudaFree(in.mem);
-  if (in.h_ctrl) cudaFreeHost(in.h_ctrl);
+  if (in.mem) {
+    if (in.async_alloc)
+      cudaFreeAsync(in.mem, in.stream);
+    else
+      cudaFree(in.mem);
+  }
+  if (in.h_ctrl && !in.h_ctrl_external) cudaFreeHost(in.h_ctrl);
   in.mem = nullptr;
   in.h_ctrl = nullptr;
 }
@@ -436,7 +480,7 @@ static ot_status issue_chunk(Context& ctx, Instance& in, int64_t count, bool cer
 }
 
 // Read the control block (certificate record, k, error bits) after the stream drains.
-static ot_status read_ctrl(Context& ctx, Instance& in) {
+ot_status read_ctrl(Context& ctx, Instance& in) {
   OT_CUDA(cudaMemcpyAsync(in.h_ctrl, in.ctrl, 16 * sizeof(double), cudaMemcpyDeviceToHost, in.stream));
   OT_CUDA(cudaStreamSynchronize(in.stream));
   const int err = ((int*)in.h_ctrl)[18];
@@ -453,7 +497,7 @@ static ot_status read_ctrl(Context& ctx, Instance& in) {
 }
 
 // Fold the certificate just read into the best-so-far bounds (App. G.3) and the retained iterate.
-static ot_status absorb_cert(Context& ctx, Instance& in) {
+ot_status absorb_cert(Context& ctx, Instance& in) {
   const double* c = in.h_ctrl;
   in.U = c[kCertU];
   in.L = c[kCertL];
@@ -472,7 +516,7 @@ static ot_status absorb_cert(Context& ctx, Instance& in) {
   return OT_OK;
 }
 
-static void fill_result(const Instance& in, ot_result* r) {
+void fill_result(const Instance& in, ot_result* r) {
   if (!r) return;
   r->iters = in.k;
   r->best_iter = in.best_iter;
@@ -489,6 +533,8 @@ static void fill_result(const Instance& in, ot_result* r) {
   r->omega = in.omega;
   r->stop = in.stop;
   r->device_errors = in.device_errors;
+  r->latency_s = 0;
+  r->queue_s = 0;
 }
 
 // Run n iterations; certificate iterations where (k+1) % cert_every == 0, plus the final iteration

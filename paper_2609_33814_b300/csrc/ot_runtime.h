@@ -48,6 +48,13 @@ struct LaunchPlan {
   int grid_row = 0, grid_col = 0;
 };
 
+// Byte offsets of an instance's buffers inside its single device allocation.
+struct Layout {
+  size_t xpack, ypack, xraw, yraw, a, b, ain, bin, la, lb, xn2, yn2, state0, fg, part, cnt, blk, ctrl, range, inst,
+      items;
+  size_t maxblk;
+};
+
 // One resident instance: descriptor, device buffers, launch plans and host-side bookkeeping.
 struct Instance {
   Inst h{};                      // host mirror of the device descriptor
@@ -67,6 +74,12 @@ struct Instance {
   int d = 0;
   int sweep_mode = 0, cert_mode = 1, exp_mode = 0;
   bool use_graphs = true;
+  // overrides used by the batched server: lane tile plans, split capacity, stream-ordered
+  // allocation and a shared pinned read-back slot
+  int force_fast_R = 0, force_fast_ch = 0, force_cert_R = 0, max_part_splits = 0;
+  bool async_alloc = false;
+  double* h_ctrl_external = nullptr;
+  Layout layout{};
   double kappa = 0, omega = 0;
   // iteration bookkeeping
   int64_t k = 0;
@@ -84,6 +97,13 @@ struct Instance {
 ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q);
 void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl);
 ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
+ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
+ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p);
+ot_status read_ctrl(Context& ctx, Instance& in);
+ot_status absorb_cert(Context& ctx, Instance& in);
+void fill_result(const Instance& in, ot_result* r);
+cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
+                         cudaStream_t stream);
 void instance_free(Instance& in);
 ot_status run_iterations(Context& ctx, Instance& in, int64_t n_iters, bool stop_rule, bool final_cert);
 ot_status standalone_certificate(Context& ctx, Instance& in);

@@ -83,14 +83,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <int MODE>
 struct PartT { typedef float4 type; };
 template <>
-struct PartT<kSweepF64> { typedef double4 type; };
+struct PartT<kSweepF64> { typedef PartF64 type; };
 
 // Partials written by other CTAs are read through L2 (the L1 of this SM is not coherent).
 __device__ __forceinline__ float4 load_part(const float4* p) { return __ldcg(p); }
-__device__ __forceinline__ double4 load_part(const double4* p) {
+__device__ __forceinline__ PartF64 load_part(const PartF64* p) {
   const double2* q = reinterpret_cast<const double2*>(p);
   const double2 a = __ldcg(q), b = __ldcg(q + 1);
-  return make_double4(a.x, a.y, b.x, b.y);
+  return PartF64{a.x, a.y, b.x, b.y};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -129,7 +129,6 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
   static_assert(UPDATE || (CERT && SIDE == 1), "a non-updating sweep is the standalone certificate");
   constexpr bool ACCN = CERT && SIDE == 1;  // accumulate N_q (Algorithm 2) on the column sweep
   typedef typename PartT<MODE>::type Part;
-  constexpr int NC = (MODE == kSweepFast) ? D + 1 : D + 2;
   constexpr uint32_t kPackTileBytes = kNComp * kTQ * 4;  // one pack tile, all components
   constexpr int kStageFloats = kStageTiles * kNComp * kTQ;
   constexpr int CH = (MODE == kSweepFast) ? CHF : 8;  // columns per chunk (one max + rescale test)

@@ -25,8 +25,8 @@ def _declared_functions():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2609_33814_b300 import build
-    path = build.build()
+    import __graft_entry__
+    path = __graft_entry__._builder().build()
     return ctypes.CDLL(path)
 
 
@@ -50,7 +50,7 @@ def test_status_strings_and_defaults(lib):
     prm = P.make_params()
     assert prm.eps0 == 1.0 and prm.lam == 1.0 and prm.cert_every == 100
     assert ctypes.sizeof(P.OtProblem) == 8 * 2 + 4 * 2 + 8 * 4 + 8 * 3
-    assert ctypes.sizeof(P.OtResult) == 8 * 3 + 8 * 10 + 4 * 2
+    assert ctypes.sizeof(P.OtResult) == 8 * 3 + 8 * 10 + 4 * 2 + 8 * 2
 
 
 def test_python_package_fails_loudly_without_library(tmp_path):
