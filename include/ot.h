@@ -222,6 +222,29 @@ ot_status ot_serve_profile_enable(ot_server* sv, int on);
 ot_status ot_serve_profile_read(ot_server* sv, int kind, int64_t* launches, double* entries, double* ms);
 void ot_serve_destroy(ot_server* sv);
 
+/* ---------------------------------------------------------------------------------------------
+ * Allocation-free row update.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory (code running under a runtime or plugin host that owns all
+ * device allocations and forbids libraries from calling cudaMalloc).  It computes one row sweep
+ * of Algorithm 1 at temperature eps,
+ *     log_alpha_hat[i] = log_r[i] - LSE_j( log_bt[j] - kappa ||x_i - y_j||^2 / eps ),
+ * with the same FP32 kernel as ot_step's fast row sweep, and allocates nothing: every buffer it
+ * needs beyond its arguments lives in a fixed scratch array of about 3.2 MB inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   - x (n x d floats), y (m x d floats), log_r (n doubles), log_bt (m doubles) are device inputs;
+ *     log_alpha_hat (n doubles) is the device output.  1 <= n, m <= OT_NOALLOC_MAX_POINTS, d in 1..3,
+ *     kappa > 0, eps > 0; anything else returns OT_EINVAL before touching the device.
+ *   - stream is a cudaStream_t (0 = the legacy default stream); the call waits for it to finish.
+ *   - The first call on a device looks the scratch address up for that device (with that device
+ *     current); make that first call before any stream capture.
+ *   - All calls share the one scratch array, which keeps the last call's contents: calls that
+ *     overlap on the GPU (from several host threads or streams) race and must not be made.
+ * Returns OT_ENUMERIC if an output is non-finite. */
+#define OT_NOALLOC_MAX_POINTS 16384
+ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, const float* x, const float* y,
+                                const double* log_r, const double* log_bt, double kappa, double eps,
+                                double* log_alpha_hat, uint64_t stream);
+
 /* Measurement support (not part of the method): kernel timing.  While enabled on a context, every
  * iteration chunk of its states records a CUDA event on the launching stream before and after each
  * sweep launch (inside the captured CUDA graph) and waits for the chunk, and per kind of sweep

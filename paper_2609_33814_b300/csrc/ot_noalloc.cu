@@ -1,0 +1,152 @@
+// An allocation-free variant of the row sweep, for callers that must not allocate device memory
+// (for example code running inside a memory-capped plugin or a runtime that owns every device
+// allocation and forbids cudaMalloc from libraries).  Everything the sweep needs beyond the
+// caller's inputs and output lives in one fixed-size scratch array in this file's device memory.
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/ot.h"
+#include "ot_kernels.cuh"
+#include "ot_runtime.h"
+
+namespace ot {
+
+cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
+                               double* n2, cudaStream_t s);
+cudaError_t launch_repack_cols(const Inst* I, int m, cudaStream_t s);
+size_t sweep_smem_bytes();
+
+namespace {
+
+constexpr int64_t kMaxPts = OT_NOALLOC_MAX_POINTS;
+constexpr int kMaxTiles = (int)((kMaxPts + kTQ - 1) / kTQ);
+constexpr int kMaxBlocks = (int)((kMaxPts + kThreads - 1) / kThreads);  // R = 1 point blocks
+constexpr int kMaxSplits = 8;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch layout (byte offsets); everything except the caller's arrays.
+constexpr size_t kOffXPack = 0;
+constexpr size_t kOffYPack = kOffXPack + align256((size_t)kMaxTiles * kNComp * kTQ * sizeof(float));
+constexpr size_t kOffXN2 = kOffYPack + align256((size_t)kMaxTiles * kNComp * kTQ * sizeof(float));
+constexpr size_t kOffYN2 = kOffXN2 + align256(kMaxPts * sizeof(double));
+constexpr size_t kOffAlpha = kOffYN2 + align256(kMaxPts * sizeof(double));
+constexpr size_t kOffTilde = kOffAlpha + align256(kMaxPts * sizeof(double));
+constexpr size_t kOffPart = kOffTilde + align256(kMaxPts * sizeof(double));
+constexpr size_t kOffCnt = kOffPart + align256((size_t)kMaxSplits * kMaxPts * sizeof(float4));
+constexpr size_t kOffCtrl = kOffCnt + align256((kMaxBlocks + 2) * sizeof(unsigned));
+constexpr size_t kOffInst = kOffCtrl + align256(16 * sizeof(double));
+constexpr size_t kOffItems = kOffInst + align256(sizeof(Inst));
+constexpr size_t kScratchBytes = kOffItems + align256((size_t)kMaxBlocks * kMaxSplits * sizeof(Item));
+
+}  // namespace
+
+// The scratch array.  Host code must not use its name as a device address: the address comes from
+// cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Writes the instance descriptor (passed by value) and the work items into the scratch.
+__global__ void noalloc_setup_kernel(Inst inst, Inst* dst, Item* items, int pblks, int splits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *dst = inst;
+  if (i < pblks * splits) items[i] = Item{0, i % pblks, i / pblks, splits};
+}
+
+static std::mutex g_mu;
+static void* g_base[256];  // scratch address per device ordinal, set on the first call
+
+}  // namespace ot
+
+using namespace ot;
+
+extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, const float* x, const float* y,
+                                           const double* log_r, const double* log_bt, double kappa, double eps,
+                                           double* log_alpha_hat, uint64_t stream) {
+  if (n < 1 || m < 1 || n > kMaxPts || m > kMaxPts) return OT_EINVAL;  // beyond the scratch capacity
+  if (d < 1 || d > 3 || !x || !y || !log_r || !log_bt || !log_alpha_hat) return OT_EINVAL;
+  if (!(kappa > 0.0) || !(eps > 0.0)) return OT_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return OT_ECUDA;
+  char* base;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_base[dev]) {
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return OT_ECUDA;
+      }
+      g_base[dev] = p;
+    }
+    base = (char*)g_base[dev];
+  }
+  cudaStream_t s = (cudaStream_t)(uintptr_t)stream;
+  const int tiles_x = (int)((n + kTQ - 1) / kTQ), tiles_y = (int)((m + kTQ - 1) / kTQ);
+  const int pblks = (int)((n + kThreads - 1) / kThreads);  // R = 1
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  SweepFn fn = get_sweep(d, kSweepFast, 1, 16, 0);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads, sweep_smem_bytes());
+  const int resident = (per_sm > 0 ? per_sm : 1) * sms;
+  int splits = (4 * resident + pblks - 1) / pblks;
+  splits = splits < 1 ? 1 : (splits > kMaxSplits ? kMaxSplits : splits);
+  if (splits > tiles_y) splits = tiles_y;
+  const int tps = (tiles_y + splits - 1) / splits;
+  splits = (tiles_y + tps - 1) / tps;
+
+  Inst h{};
+  h.n = (int)n;
+  h.m = (int)m;
+  h.d = d;
+  h.tiles_x = tiles_x;
+  h.tiles_y = tiles_y;
+  h.pblk_x = pblks;
+  h.kappa = kappa;
+  h.eta = eps;       // k = 0 and lambda = 1 give the sweep temperature eta / (lambda k + 1) = eps
+  h.lambda = 1.0;
+  h.omega = 1.0;
+  h.xpack = (float*)(base + kOffXPack);
+  h.ypack = (float*)(base + kOffYPack);
+  h.log_a = log_r;
+  h.log_b = nullptr;
+  h.xn2 = (const double*)(base + kOffXN2);
+  h.yn2 = (const double*)(base + kOffYN2);
+  h.log_alpha = (double*)(base + kOffAlpha);
+  h.log_alpha_hat = log_alpha_hat;
+  h.log_beta = const_cast<double*>(log_bt);        // read only: beta^{k-1} = beta^{k-2} = beta-tilde
+  h.log_beta_prev = const_cast<double*>(log_bt);
+  h.log_beta_tilde_next = (double*)(base + kOffTilde);
+  h.part = base + kOffPart;
+  h.cnt = (unsigned*)(base + kOffCnt);
+  h.done = h.cnt + kMaxBlocks;
+  double* ctrl = (double*)(base + kOffCtrl);
+  h.cert = ctrl;
+  h.k = (long long*)(ctrl + 8);
+  h.err = (int*)(ctrl + 9);
+  Inst* d_inst = (Inst*)(base + kOffInst);
+  Item* d_items = (Item*)(base + kOffItems);
+
+  // every call shares the scratch: clear the counters, k, the error bits and the relaxation input
+  if (cudaMemsetAsync(h.cnt, 0, (kMaxBlocks + 2) * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(ctrl, 0, 16 * sizeof(double), s) != cudaSuccess ||
+      cudaMemsetAsync(h.log_alpha, 0, n * sizeof(double), s) != cudaSuccess)
+    return OT_ECUDA;
+  const int nitems = pblks * splits;
+  noalloc_setup_kernel<<<(nitems + 255) / 256, 256, 0, s>>>(h, d_inst, d_items, pblks, splits);
+  if (cudaGetLastError() != cudaSuccess) return OT_ECUDA;
+  if (launch_pack_coords(x, (int)n, d, tiles_x, kappa, h.xpack, (double*)h.xn2, s) != cudaSuccess ||
+      launch_pack_coords(y, (int)m, d, tiles_y, kappa, h.ypack, (double*)h.yn2, s) != cudaSuccess ||
+      launch_repack_cols(d_inst, (int)m, s) != cudaSuccess)
+    return OT_ECUDA;
+  const int grid = nitems < resident ? nitems : resident;
+  if (launch_sweep(fn, d_inst, d_items, nitems, grid, s) != cudaSuccess) return OT_ECUDA;
+  int err = 0;
+  if (cudaMemcpyAsync(&err, h.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return OT_ECUDA;
+  if (err & kErrTimeout) return OT_ETIMEDOUT;
+  if (err & kErrNonFinite) return OT_ENUMERIC;
+  return OT_OK;
+}
