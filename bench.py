@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--engine", default="batched", choices=["batched", "serial"])
     ap.add_argument("--slots", type=int, default=256, help="server slots (batched engine)")
+    ap.add_argument("--serial-steps", type=int, default=1,
+                    help="also time this many steps of one-at-a-time solves (same stop rule) for comparison")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--rate", type=float, default=32.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--max-iters", type=int, default=2000)
@@ -51,6 +53,13 @@ def parse():
     ap.add_argument("--tol-rel", type=float, default=0.01)
     ap.add_argument("--seed", type=int, default=2609)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--workload", default="serve", choices=["serve", "sweep"],
+                    help="serve: the serving stream (the bench line); sweep: one resident instance, "
+                         "fast iterations only (kernel roofline and profiling)")
+    ap.add_argument("--size", type=int, default=512, help="sweep workload: s for an s x s grid, or -n for "
+                                                          "n RGB points")
+    ap.add_argument("--iters", type=int, default=10, help="sweep workload: iterations per step")
+    ap.add_argument("--precision", default="mufu", choices=["mufu", "comp", "fp64"])
     return ap.parse_args()
 
 
@@ -125,7 +134,7 @@ def run_serial(ctx, reqs, probs, dev_inputs, args, host: bool):
     """One-at-a-time FIFO serving: each request starts at max(arrival, previous completion)."""
     import torch
     t0 = time.perf_counter()
-    lat, ttg, entries, conv = [], [], 0.0, 0
+    lat, ttg, entries, conv, ttg_conv = [], [], 0.0, 0, []
     h2d = d2h = 0
     for r, p, dv in zip(reqs, probs, dev_inputs):
         now = time.perf_counter() - t0
@@ -146,7 +155,9 @@ def run_serial(ctx, reqs, probs, dev_inputs, args, host: bool):
         ttg.append(te - ts)
         entries += 2.0 * p.n * p.m * res["iters"]
         conv += res["stop"] == "tol"
-    return dict(latency=lat, ttg=ttg, entries=entries, converged=conv, h2d=h2d, d2h=d2h)
+        if res["stop"] == "tol":
+            ttg_conv.append(te - ts)
+    return dict(latency=lat, ttg=ttg, entries=entries, converged=conv, h2d=h2d, d2h=d2h, ttg_conv=ttg_conv)
 
 
 def run_batched(srv, reqs, probs, dev_inputs, args, host: bool):
@@ -167,7 +178,7 @@ def run_batched(srv, reqs, probs, dev_inputs, args, host: bool):
             x, y, a, b = dv
             ids.append(srv.submit(x, y, a, b, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15,
                                   **solve_params(args)))
-    lat, ttg, entries, conv = [], [], 0.0, 0
+    lat, ttg, entries, conv, ttg_conv = [], [], 0.0, 0, []
     for rid, p in zip(ids, probs):
         f, g, res = srv.wait(rid, -1.0)
         d2h += f.nbytes + g.nbytes
@@ -175,7 +186,9 @@ def run_batched(srv, reqs, probs, dev_inputs, args, host: bool):
         ttg.append(res["latency_s"] - res["queue_s"])
         entries += 2.0 * p.n * p.m * res["iters"]
         conv += res["stop"] == "tol"
-    return dict(latency=lat, ttg=ttg, entries=entries, converged=conv, h2d=h2d, d2h=d2h)
+        if res["stop"] == "tol":
+            ttg_conv.append(res["latency_s"] - res["queue_s"])
+    return dict(latency=lat, ttg=ttg, entries=entries, converged=conv, h2d=h2d, d2h=d2h, ttg_conv=ttg_conv)
 
 
 def flush_l2(buf):
@@ -343,6 +356,24 @@ def run_ours(args, rank: int, world: int):
         e2e_times.append(time.perf_counter() - t)
         e2e_res.append(r2)
 
+    serial = None
+    if args.engine == "batched" and args.serial_steps > 0:
+        st_t, st_r = [], None
+        for _ in range(args.serial_steps):
+            flush_l2(l2buf)
+            barrier()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            st_r = run_serial(ctx, reqs, probs, dev_inputs, args, host=False)
+            ev1.record()
+            barrier()
+            st_t.append(ev0.elapsed_time(ev1) / 1e3)
+        serial = {"value": st_r["entries"] / max(st_t), "unit": UNIT, "ms_per_step": 1e3 * max(st_t),
+                  "p50_latency_s": float(np.percentile(st_r["latency"], 50)),
+                  "p99_latency_s": float(np.percentile(st_r["latency"], 99)),
+                  "converged_frac": st_r["converged"] / len(st_r["latency"]),
+                  "note": "same requests solved one at a time with ot_solve (no batching); the results are "
+                          "bitwise identical to the batched ones, so the certified gaps are equal"}
     t_step = max(step_times)
     entries = sum(r["entries"] for r in results) / len(results)
     if dist:
@@ -381,6 +412,9 @@ def run_ours(args, rank: int, world: int):
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
         "time_to_gap_median_s": float(np.median(ttg)), "time_to_gap_p99_s": float(np.percentile(ttg, 99)),
         "converged_frac": results[-1]["converged"] / len(lat),
+        "time_to_gap_converged_median_s": (float(np.median(results[-1]["ttg_conv"]))
+                                           if results[-1]["ttg_conv"] else None),
+        "serial_baseline": serial,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "entries/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": None,
                      "kernel": "fast sweep (row + column launches)", "launches": fast_n,
@@ -401,10 +435,58 @@ def run_ours(args, rank: int, world: int):
         td.barrier()
 
 
+def run_sweep(args):
+    """One resident instance, fast iterations only: entries/s of the sweep kernels alone."""
+    import ctypes
+    import torch
+    import paper_2609_33814_b300 as P
+    prob = I.grid_problem(args.size, args.seed) if args.size > 0 else I.rgb_problem(-args.size, args.seed)
+    ctx = P.Context(0)
+    lib = P.lib()
+    dev = [torch.from_numpy(v).cuda() for v in (prob.x, prob.y, prob.a, prob.b)]
+    S = ctx.state(*dev, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0 if args.size > 0 else 0.1,
+                  precision=args.precision, cert_every=0)
+    for _ in range(args.warmup):
+        S.step(args.iters)
+    clock = ClockSampler(0)
+    clock.start()
+    lib.ot_profile_reset(ctx.handle)
+    lib.ot_profile_enable(ctx.handle, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        S.step(args.iters)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    lib.ot_profile_enable(ctx.handle, 0)
+    clocks = clock.stop()
+    n = ctypes.c_int64(); e = ctypes.c_double(); ms = ctypes.c_double()
+    tot_n, tot_e, tot_ms = 0, 0.0, 0.0
+    for kind in (0, 1):
+        lib.ot_profile_read(ctx.handle, kind, ctypes.byref(n), ctypes.byref(e), ctypes.byref(ms))
+        tot_n += n.value; tot_e += e.value; tot_ms += ms.value
+    achieved = tot_e / (tot_ms / 1e3)
+    d = prob.d
+    peak = min(128.0 / (d + 2), 32.0) * 148 * (clocks.get("sm_max_mhz") or 2032.0) * 1e6
+    out = {"metric": "implicit entries/s per dual sweep (one resident instance)", "value": achieved,
+           "unit": "entries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+           "config": {"workload": f"{'grid %dx%d' % (args.size, args.size) if args.size > 0 else 'rgb %d' % -args.size}"
+                                  f" d={d}, {args.iters} iterations per step", "n": prob.n, "m": prob.m},
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "entries/s",
+                        "frac": achieved / peak, "traffic": None, "launches": tot_n,
+                        "avg_launch_ms": tot_ms / max(tot_n, 1)},
+           "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.workload == "sweep":
+        run_sweep(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -56,54 +56,79 @@ int Context::resident_ctas(SweepFn fn) {
 // ---------------------------------------------------------------------------------------------
 // Launch plans: points per thread R, chunk width and the split counts of both sweeps.
 // ---------------------------------------------------------------------------------------------
-static int split_count(int pblks, int qtiles, int target_items) {
-  int s = std::max(1, std::min(qtiles, (target_items + pblks - 1) / pblks));
-  const int tps = (qtiles + s - 1) / s;
-  return (qtiles + tps - 1) / tps;  // no empty split
-}
-
+constexpr int kMaxSplits = 64;      // split cap: bounds the partial buffer and the epilogue merge
+constexpr int kMinSplitTiles = 16;  // a split covers at least 16 tiles (2048 points): keeps the fixed
+                                    // per-item costs small next to the item's work
 static int env_int(const char* name, int dflt) {
   const char* v = getenv(name);
   return v && *v ? atoi(v) : dflt;
 }
 
-void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl) {
-  const int np = (int)std::max(in.n, in.m);
-  int R, ch = 8;
-  const bool is_fast_plan = &pl == &in.fast;
+// The plan that fixes an instance's numerics: points per thread R and chunk width CH depend only on
+// (d, precision mode), the split counts only on the instance's own sizes.  An instance therefore
+// produces bitwise the same results alone or inside any batch; only the launch grid (which does
+// not affect results) depends on the device's occupancy.
+void canonical_tile(int d, int mode, int* R, int* ch) {
   if (mode == kSweepF64) {
-    R = np >= ctx.sms * kThreads * 4 ? 2 : 1;
+    *R = 1;
+    *ch = 8;
   } else if (mode == kSweepComp) {
-    R = np >= ctx.sms * kThreads * 8 ? 4 : (np >= ctx.sms * kThreads * 2 ? 2 : 1);
+    *R = 2;
+    *ch = 8;
+  } else if (d == 3) {
+    *R = 2;
+    *ch = 16;
   } else {
-    R = np >= ctx.sms * kThreads * 8 ? 4 : (np >= ctx.sms * kThreads * 2 ? 2 : 1);
-    ch = R <= 2 ? 16 : 16;
-    // tuning overrides (experiments): OT_FORCE_R, OT_FORCE_CH
+    *R = 4;
+    *ch = 8;
+  }
+}
+
+// Split count of one sweep of an instance: among the counts that leave every split at least
+// kMinSplitTiles tiles, the smallest whose work items (point blocks x splits, all the same size)
+// fill close to a whole number of waves of the kernel's resident CTAs, so that the last wave is
+// not left mostly idle.  It depends only on the instance's sizes and the device's resident-CTA
+// count, never on what else runs in the same launch.
+int canonical_splits(int64_t np, int64_t nq, int R, int resident) {
+  const int pblks = (int)((np + kThreads * R - 1) / (kThreads * R));
+  const int qtiles = (int)((nq + kTQ - 1) / kTQ);
+  int best = 1;
+  double best_eff = -1.0;
+  const int smax = std::max(1, std::min(kMaxSplits, qtiles / kMinSplitTiles));
+  for (int s = 1; s <= smax; ++s) {
+    const int tps = (qtiles + s - 1) / s;
+    const int sp = (qtiles + tps - 1) / tps;  // no empty split
+    if (sp != s) continue;
+    const double waves = (double)pblks * sp / resident;
+    const double eff = waves / std::ceil(waves);
+    if (eff >= 0.95 && waves >= 1.0) return sp;
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = sp;
+    }
+  }
+  return best;
+}
+
+void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl) {
+  int R, ch;
+  canonical_tile(in.d, mode, &R, &ch);
+  // tuning overrides for experiments (they change the numerics): OT_FORCE_R, OT_FORCE_CH
+  if (mode == kSweepFast) {
     R = env_int("OT_FORCE_R", R);
     ch = env_int("OT_FORCE_CH", ch);
   }
-  if (is_fast_plan && in.force_fast_R > 0) {
-    R = in.force_fast_R;
-    ch = in.force_fast_ch > 0 ? in.force_fast_ch : ch;
-  }
-  if (!is_fast_plan && in.force_cert_R > 0) R = in.force_cert_R;
-  if (!get_sweep(in.d, mode, R, ch, 0)) {
-    R = 1;
-    ch = 16;
-  }
+  if (!get_sweep(in.d, mode, R, ch, 0)) canonical_tile(in.d, mode, &R, &ch);
   pl.mode = mode;
   pl.R = R;
   pl.ch = ch;
   const int rpb = kThreads * R;
   pl.pblk_row = (int)((in.n + rpb - 1) / rpb);
   pl.pblk_col = (int)((in.m + rpb - 1) / rpb);
-  const int tiles_x = (int)((in.n + kTQ - 1) / kTQ), tiles_y = (int)((in.m + kTQ - 1) / kTQ);
   SweepFn fn = get_sweep(in.d, mode, R, ch, 0);
   const int resident = ctx.resident_ctas(fn);
-  const int target = env_int("OT_FORCE_ITEMS", 4 * resident);
-  const int fs = env_int("OT_FORCE_SPLITS", 0);
-  pl.splits_row = fs > 0 ? split_count(1, tiles_y, fs) : split_count(pl.pblk_row, tiles_y, target);
-  pl.splits_col = fs > 0 ? split_count(1, tiles_x, fs) : split_count(pl.pblk_col, tiles_x, target);
+  pl.splits_row = canonical_splits(in.n, in.m, R, resident);
+  pl.splits_col = canonical_splits(in.m, in.n, R, resident);
   pl.n_row = pl.pblk_row * pl.splits_row;
   pl.n_col = pl.pblk_col * pl.splits_col;
   pl.grid_row = std::min(pl.n_row, resident);
@@ -214,9 +239,6 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   size_t nsp = 0;
   for (const LaunchPlan* pl : {&in.fast, &in.cert})
     nsp = std::max(nsp, std::max((size_t)pl->splits_row * n, (size_t)pl->splits_col * m));
-  if (in.max_part_splits > 0)
-    nsp = std::max(nsp, std::max((size_t)std::min(in.max_part_splits, h.tiles_y) * n,
-                                 (size_t)std::min(in.max_part_splits, h.tiles_x) * m));
   const size_t maxblk = (std::max(n, m) + kThreads - 1) / kThreads;
   Layout& L = in.layout;
   Carve cv;

@@ -74,9 +74,7 @@ struct Instance {
   int d = 0;
   int sweep_mode = 0, cert_mode = 1, exp_mode = 0;
   bool use_graphs = true;
-  // overrides used by the batched server: lane tile plans, split capacity, stream-ordered
-  // allocation and a shared pinned read-back slot
-  int force_fast_R = 0, force_fast_ch = 0, force_cert_R = 0, max_part_splits = 0;
+  // used by the batched server: stream-ordered allocation and a shared pinned read-back slot
   bool async_alloc = false;
   double* h_ctrl_external = nullptr;
   Layout layout{};
@@ -96,6 +94,7 @@ struct Instance {
 
 ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q);
 void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl);
+void canonical_tile(int d, int mode, int* R, int* ch);
 ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
 ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
 ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p);

@@ -86,7 +86,6 @@ struct Server {
   uint64_t next_id = 1;
   double* h_ctrl_pool = nullptr;
   std::vector<int> free_ctrl;
-  int max_part_splits = 16;
   // statistics since the last reset
   std::vector<double> latencies;
   int64_t submitted = 0, completed = 0, cancelled = 0, failed = 0, chunks = 0;
@@ -118,15 +117,9 @@ int Server::lane_for(const Request* r) {
   L.mode = mode;
   L.cert_mode = mode == kSweepF64 ? kSweepF64 : kSweepComp;
   L.ce = r->params.cert_every;
-  if (mode == kSweepF64) {
-    L.R_fast = 1;
-    L.ch_fast = 8;
-    L.R_cert = 1;
-  } else if (mode == kSweepComp) {
-    L.R_fast = 2;
-    L.ch_fast = 8;
-    L.R_cert = 2;
-  }
+  int ch_cert = 8;
+  canonical_tile(L.d, L.mode, &L.R_fast, &L.ch_fast);
+  canonical_tile(L.d, L.cert_mode, &L.R_cert, &ch_cert);
   return nlanes++;
 }
 
@@ -206,27 +199,26 @@ void Server::run_chunk(Lane& L) {
       const bool row = kind % 2 == 0;
       SweepFn fn = get_sweep(L.d, mode_of[kind], R, kind < 2 ? L.ch_fast : 8, 0);
       const int resident = ctx.resident_ctas(fn);
-      // equal-sized items across instances: one split length (in tiles) for the whole lane
-      double work = 0;
-      for (size_t i = 0; i < na; ++i) {
-        const Instance& in = *L.active[i]->inst;
-        const int64_t np = row ? in.n : in.m, nq = row ? in.m : in.n;
-        work += (double)((np + kThreads * R - 1) / (kThreads * R)) * (double)((nq + kTQ - 1) / kTQ);
-      }
-      const double target = 4.0 * resident;
-      const int tps_lane = std::max(1, (int)std::ceil(work / target));
+      // each instance contributes its own work items (its plan fixes its numerics)
       L.off[kind] = (int)items.size();
       for (size_t i = 0; i < na; ++i) {
         const Instance& in = *L.active[i]->inst;
-        const int64_t np = row ? in.n : in.m, nq = row ? in.m : in.n;
-        const int pblks = (int)((np + kThreads * R - 1) / (kThreads * R));
-        const int qtiles = (int)((nq + kTQ - 1) / kTQ);
-        int splits = std::max(1, std::min({qtiles, max_part_splits, (qtiles + tps_lane - 1) / tps_lane}));
-        const int tps = (qtiles + splits - 1) / splits;
-        splits = (qtiles + tps - 1) / tps;
+        const LaunchPlan& pl = kind < 2 ? in.fast : in.cert;
+        const int pblks = row ? pl.pblk_row : pl.pblk_col;
+        const int splits = row ? pl.splits_row : pl.splits_col;
         for (int sp = 0; sp < splits; ++sp)
           for (int b = 0; b < pblks; ++b) items.push_back(Item{(int)i, b, sp, splits});
       }
+      // longest items first: CTAs take items with a fixed stride, so this evens out their loads
+      auto work_of = [&](const Item& it) {
+        const Instance& in = *L.active[it.inst]->inst;
+        const int64_t nq = row ? in.m : in.n;
+        const int qtiles = (int)((nq + kTQ - 1) / kTQ);
+        const int tps = (qtiles + it.nsplit - 1) / it.nsplit;
+        return std::min(tps, qtiles - it.split * tps);
+      };
+      std::stable_sort(items.begin() + L.off[kind], items.end(),
+                       [&](const Item& a, const Item& b) { return work_of(a) > work_of(b); });
       L.cnt[kind] = (int)items.size() - L.off[kind];
       L.grid[kind] = std::min(L.cnt[kind], resident);
     }
@@ -365,6 +357,10 @@ void Server::loop() {
     for (Request* r : to_admit) {
       if (admit(r)) {
         Lane& L = lanes[r->lane];
+        // every instance of a lane has the same (d, precision) and hence the same tile plans
+        L.R_fast = r->inst->fast.R;
+        L.ch_fast = r->inst->fast.ch;
+        L.R_cert = r->inst->cert.R;
         L.active.push_back(r);
         L.dirty = true;
       }
@@ -558,16 +554,9 @@ ot_status ot_serve_submit(ot_server* sv, const ot_problem* prob, const ot_params
   r->inst = new Instance();
   r->inst->async_alloc = true;
   r->inst->use_graphs = false;
-  r->inst->max_part_splits = S.max_part_splits;
   r->lane = S.lane_for(r);
   ot_status st = r->lane < 0 ? OT_EINVAL : OT_OK;
-  if (st == OT_OK) {
-    const Lane& L = S.lanes[r->lane];
-    r->inst->force_fast_R = L.R_fast;
-    r->inst->force_fast_ch = L.ch_fast;
-    r->inst->force_cert_R = L.R_cert;
-    st = instance_prepare(S.ctx, *r->inst, &r->prob, &r->params, S.ctx.stream);
-  }
+  if (st == OT_OK) st = instance_prepare(S.ctx, *r->inst, &r->prob, &r->params, S.ctx.stream);
   r->bytes = r->inst->bytes;
   if (st == OT_OK && r->bytes > S.budget) st = OT_ENOMEM;
   if (st != OT_OK) {

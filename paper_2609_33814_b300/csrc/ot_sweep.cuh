@@ -147,7 +147,41 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
   }
   __syncthreads();
 
-  uint32_t gstage = 0;  // pipeline stages consumed by this CTA so far (stage index and parity)
+  // The TMA pipeline runs across work items: thread 0 keeps kStages stages in flight, moving on to
+  // the CTA's next item (it + gridDim.x) before the current one ends, so it never drains.
+  uint32_t gcons = 0;  // stages consumed by this CTA (stage slot and mbarrier parity)
+  uint32_t gprod = 0;  // stages issued by this CTA
+  int pr_it = blockIdx.x, pr_us = 0, pr_nst = 0, pr_qt0 = 0, pr_ntl = 0;
+  const float* pr_qpack = nullptr;
+  auto pr_load = [&]() {
+    if (pr_it >= nitems) return;
+    const Item itp = items[pr_it];
+    const Inst* Ip = insts + itp.inst;
+    const int qtl = SIDE == 0 ? Ip->tiles_y : Ip->tiles_x;
+    const int tpsp = (qtl + itp.nsplit - 1) / itp.nsplit;
+    pr_qt0 = itp.split * tpsp;
+    pr_ntl = min(qtl, pr_qt0 + tpsp) - pr_qt0;
+    pr_nst = (pr_ntl + kStageTiles - 1) / kStageTiles;
+    pr_qpack = SIDE == 0 ? Ip->ypack : Ip->xpack;
+    pr_us = 0;
+  };
+  auto produce = [&]() {
+    if (pr_it >= nitems) return;
+    const int stg = gprod % kStages;
+    const int tiles = min(kStageTiles, pr_ntl - pr_us * kStageTiles);
+    mbar_expect_tx(&bars[stg], tiles * kPackTileBytes);
+    bulk_g2s(smem + stg * kStageFloats, pr_qpack + (size_t)(pr_qt0 + pr_us * kStageTiles) * kNComp * kTQ,
+             tiles * kPackTileBytes, &bars[stg]);
+    ++gprod;
+    if (++pr_us == pr_nst) {
+      pr_it += gridDim.x;
+      pr_load();
+    }
+  };
+  if (tid == 0) {
+    pr_load();
+    for (int j = 0; j < kStages; ++j) produce();
+  }
 
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const Item item = items[it];
@@ -209,22 +243,11 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
         for (int k = 0; k < D; ++k) A2[r][k] = pk2(Ah[r][k], Ah[r][k]);
     }
 
-    // ---- pipeline prologue: each stage holds up to kStageTiles consecutive pack tiles ----
-    const int nst = (ntl + kStageTiles - 1) / kStageTiles;
-    if (tid == 0) {
-      const int pre = min(nst, kStages);
-      for (int j = 0; j < pre; ++j) {
-        const int stg = (gstage + j) % kStages;
-        const int tiles = min(kStageTiles, ntl - j * kStageTiles);
-        mbar_expect_tx(&bars[stg], tiles * kPackTileBytes);
-        bulk_g2s(smem + stg * kStageFloats, qpack + (size_t)(qt0 + j * kStageTiles) * kNComp * kTQ,
-                 tiles * kPackTileBytes, &bars[stg]);
-      }
-    }
+    const int nst = (ntl + kStageTiles - 1) / kStageTiles;  // pipeline stages of this item
 
     bool fresh = true;
     for (int us = 0; us < nst; ++us) {
-      const uint32_t g = gstage + us;
+      const uint32_t g = gcons + us;
       const int stg = g % kStages;
       const uint32_t par = (g / kStages) & 1u;
       const bool ok = mbar_wait_bounded(&bars[stg], par, kWaitLimit);
@@ -303,8 +326,8 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
           }
           fresh = false;
         };
-        // exp2 and a pairwise (tree) sum of the chunk, then one add into the running pair sum
-        auto accumulate = [&](u64 (&v)[R][CH / 2]) {
+        // exp2 and a pairwise (tree) sum of the chunk per point
+        auto chunk_sums = [&](u64 (&v)[R][CH / 2], u64 (&cs)[R]) {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             u64 e[CH / 2];
@@ -318,14 +341,33 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
             for (int w = 1; w < CH / 2; w *= 2)
 #pragma unroll
               for (int j = 0; j + w < CH / 2; j += 2 * w) e[j] = add2(e[j], e[j + w]);
-            st.acc[r] = add2(st.acc[r], e[0]);
+            cs[r] = e[0];
           }
         };
+        // The running shift only has to stay within ~64 (base 2) of the largest value seen, so
+        // instead of a per-entry maximum each chunk's sum is tested once: a sum above 2^64
+        // (or an overflow to infinity) sends the chunk through the exact maximum, an exact
+        // power-of-two rescale of the running sums, and a second exp2 pass.  The first chunk of
+        // a work item always takes the exact maximum to set the shift.
 #pragma unroll 1
         for (int c0 = 0; c0 < kTQ; c0 += CH) {
           exponents(va, c0);
-          rescale(va);
-          accumulate(va);
+          if (fresh) rescale(va);
+          u64 cs[R];
+          chunk_sums(va, cs);
+          bool big = false;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            float lo, hi;
+            up2(cs[r], lo, hi);
+            big |= !(lo + hi <= 0x1p64f) && (lo + hi == lo + hi);  // > 2^64 or +inf, not NaN
+          }
+          if (__any_sync(0xffffffffu, big)) {
+            rescale(va);
+            chunk_sums(va, cs);
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) st.acc[r] = add2(st.acc[r], cs[r]);
         }
         // fold the tile's pair sums into the compensated running sum
 #pragma unroll
@@ -454,22 +496,14 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
         if (tid == 0) {
           atomicOr(I->err, kErrTimeout);
           // let the copies already in flight land before the CTA's shared memory is released
-          for (int j = us + 1; j < min(nst, us + kStages); ++j) {
-            const uint32_t gj = gstage + j;
+          for (uint32_t gj = g + 1; gj < gprod; ++gj)
             mbar_wait_bounded(&bars[gj % kStages], (gj / kStages) & 1u, kWaitLimit);
-          }
         }
         return;
       }
-      if (tid == 0 && us + kStages < nst) {
-        const int j = us + kStages;
-        const int tiles = min(kStageTiles, ntl - j * kStageTiles);
-        mbar_expect_tx(&bars[stg], tiles * kPackTileBytes);
-        bulk_g2s(smem + stg * kStageFloats, qpack + (size_t)(qt0 + j * kStageTiles) * kNComp * kTQ,
-                 tiles * kPackTileBytes, &bars[stg]);
-      }
+      if (tid == 0) produce();  // refill the slot just consumed (possibly with the next item's tiles)
     }
-    gstage += nst;
+    gcons += nst;
 
     // ---- write this split's partials ----
     Part* part = reinterpret_cast<Part*>(I->part);
@@ -526,7 +560,16 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
           }
         }
       }
-      const double lse2 = mx + log2(S);
+      double lse2;
+      if constexpr (MODE == kSweepFast) {
+        // log2 S = exponent + log2(mantissa): the FP32 sweep's own rounding (~1e-7) dominates the
+        // FP32 log2 of the mantissa, and B300's FP64 pipe is slow
+        int ex;
+        const double mant = frexp(S, &ex);
+        lse2 = mx + (double)ex + (double)__log2f((float)mant);
+      } else {
+        lse2 = mx + log2(S);
+      }
       if constexpr (SIDE == 0) {
         const double lse = lse2 * kLn2 - I->xn2[p] * inv_eps;
         const double lah = I->log_a[p] - lse;
