@@ -48,6 +48,7 @@ def parse():
                     help="also time this many steps of one-at-a-time solves (same stop rule) for comparison")
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--rate", type=float, default=32.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--burst", action="store_true", help="every request arrives at t = 0 (profiling)")
     ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--cert-every", type=int, default=100)
     ap.add_argument("--tol-rel", type=float, default=0.01)
@@ -121,6 +122,9 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 def make_stream(args, rank: int):
     reqs = I.serving_stream(args.requests, args.seed + 7919 * rank, args.rate)
+    if args.burst:
+        for r in reqs:
+            r.arrival_s = 0.0
     probs = [I.request_problem(r) for r in reqs]
     return reqs, probs
 

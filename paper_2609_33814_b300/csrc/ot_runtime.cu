@@ -76,11 +76,11 @@ void canonical_tile(int d, int mode, int* R, int* ch) {
     *R = 2;
     *ch = 8;
   } else if (d == 3) {
-    *R = 2;
+    *R = 4;
     *ch = 16;
   } else {
-    *R = 4;
-    *ch = 8;
+    *R = 2;
+    *ch = 16;
   }
 }
 

@@ -191,7 +191,6 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
     const int splits = item.nsplit;
     const int pblks = (np + kThreads * R - 1) / (kThreads * R);
     const float* __restrict__ ppack = SIDE == 0 ? I->xpack : I->ypack;
-    const float* __restrict__ qpack = SIDE == 0 ? I->ypack : I->xpack;
     const int tps = (qtiles + splits - 1) / splits;
     const int qt0 = item.split * tps;
     const int qt1 = min(qtiles, qt0 + tps);
@@ -344,30 +343,40 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
             cs[r] = e[0];
           }
         };
-        // The running shift only has to stay within ~64 (base 2) of the largest value seen, so
-        // instead of a per-entry maximum each chunk's sum is tested once: a sum above 2^64
-        // (or an overflow to infinity) sends the chunk through the exact maximum, an exact
-        // power-of-two rescale of the running sums, and a second exp2 pass.  The first chunk of
-        // a work item always takes the exact maximum to set the shift.
+        // The running shift only has to stay within ~64 (base 2) of the largest value seen, so the
+        // tile is first run with no maximum at all (exponent FMAs, exp2, pairwise sums); only the
+        // first chunk of a work item takes the exact maximum to set the shift.  If the tile's sum
+        // then exceeds 2^64 (or overflowed), the tile, still in shared memory, is recomputed chunk
+        // by chunk with the exact maximum and an exact power-of-two rescale of the running sums.
 #pragma unroll 1
         for (int c0 = 0; c0 < kTQ; c0 += CH) {
           exponents(va, c0);
           if (fresh) rescale(va);
           u64 cs[R];
           chunk_sums(va, cs);
-          bool big = false;
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            float lo, hi;
-            up2(cs[r], lo, hi);
-            big |= !(lo + hi <= 0x1p64f) && (lo + hi == lo + hi);  // > 2^64 or +inf, not NaN
-          }
-          if (__any_sync(0xffffffffu, big)) {
-            rescale(va);
-            chunk_sums(va, cs);
-          }
 #pragma unroll
           for (int r = 0; r < R; ++r) st.acc[r] = add2(st.acc[r], cs[r]);
+        }
+        bool big = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float lo, hi;
+          up2(st.acc[r], lo, hi);
+          const float t = lo + hi;
+          big |= !(t <= 0x1p64f) && (t == t);  // above 2^64 or +inf (a NaN is left to propagate)
+        }
+        if (__any_sync(0xffffffffu, big)) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) st.acc[r] = 0ull;
+#pragma unroll 1
+          for (int c0 = 0; c0 < kTQ; c0 += CH) {
+            exponents(va, c0);
+            rescale(va);
+            u64 cs[R];
+            chunk_sums(va, cs);
+#pragma unroll
+            for (int r = 0; r < R; ++r) st.acc[r] = add2(st.acc[r], cs[r]);
+          }
         }
         // fold the tile's pair sums into the compensated running sum
 #pragma unroll
