@@ -36,6 +36,12 @@ struct Inst {
   int n, m, d;
   int tiles_x, tiles_y;          // ceil(n / kTQ), ceil(m / kTQ)
   int pblk_x;                    // point blocks of the certificate row sweep (layout of blk)
+  // Micro-splits of the reduced side, per plan (0: fast iterations, 1: certificate iterations)
+  // and sweep (0 row, 1 column): the reduced side's tiles are cut into nms runs of ms_tiles tiles
+  // (the last may be shorter), one split partial each.  They are fixed per instance, so its
+  // results do not depend on how a launch groups micro-splits into work items.
+  int nms[2][2];
+  int ms_tiles[2][2];
   double kappa, eta, lambda, omega;
   float* xpack;                  // [tiles_x][kNComp][kTQ]
   float* ypack;                  // [tiles_y][kNComp][kTQ]
@@ -68,10 +74,10 @@ struct alignas(32) PartF64 {
   double x, y, z, w;
 };
 
-// A unit of sweep work: instance, point block, split of the other side, and the split count of
-// that instance in this launch (the point-block size is kThreads * R of the launched kernel).
+// A unit of sweep work: instance, point block (kThreads * R points of the launched kernel), and a
+// run of consecutive micro-splits of the reduced side: first one and count.
 struct Item {
-  int inst, pblk, split, nsplit;
+  int inst, pblk, ms0, nms;
 };
 
 }  // namespace ot

@@ -49,7 +49,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 __global__ void noalloc_setup_kernel(Inst inst, Inst* dst, Item* items, int pblks, int splits) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) *dst = inst;
-  if (i < pblks * splits) items[i] = Item{0, i % pblks, i / pblks, splits};
+  if (i < pblks * splits) items[i] = Item{0, i % pblks, i / pblks, 1};
 }
 
 static std::mutex g_mu;
@@ -93,7 +93,8 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
   int splits = (4 * resident + pblks - 1) / pblks;
   splits = splits < 1 ? 1 : (splits > kMaxSplits ? kMaxSplits : splits);
   if (splits > tiles_y) splits = tiles_y;
-  const int tps = (tiles_y + splits - 1) / splits;
+  int tps = (tiles_y + splits - 1) / splits;
+  if (splits > 1 && (tps & 1)) ++tps;  // runs of an even number of tiles (pipeline stages of two)
   splits = (tiles_y + tps - 1) / tps;
 
   Inst h{};
@@ -103,6 +104,8 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
   h.tiles_x = tiles_x;
   h.tiles_y = tiles_y;
   h.pblk_x = pblks;
+  h.nms[0][0] = splits;  // fast row sweep: one micro-split per split
+  h.ms_tiles[0][0] = tps;
   h.kappa = kappa;
   h.eta = eps;       // k = 0 and lambda = 1 give the sweep temperature eta / (lambda k + 1) = eps
   h.lambda = 1.0;

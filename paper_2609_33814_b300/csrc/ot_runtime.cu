@@ -57,8 +57,7 @@ int Context::resident_ctas(SweepFn fn) {
 // Launch plans: points per thread R, chunk width and the split counts of both sweeps.
 // ---------------------------------------------------------------------------------------------
 constexpr int kMaxSplits = 64;      // split cap: bounds the partial buffer and the epilogue merge
-constexpr int kMinSplitTiles = 16;  // a split covers at least 16 tiles (2048 points): keeps the fixed
-                                    // per-item costs small next to the item's work
+constexpr int kMinSplitTiles = 4;   // a micro-split covers at least 4 tiles (512 points)
 static int env_int(const char* name, int dflt) {
   const char* v = getenv(name);
   return v && *v ? atoi(v) : dflt;
@@ -84,27 +83,38 @@ void canonical_tile(int d, int mode, int* R, int* ch) {
   }
 }
 
-// Split count of one sweep of an instance: among the counts that leave every split at least
-// kMinSplitTiles tiles, the smallest whose work items (point blocks x splits, all the same size)
-// fill close to a whole number of waves of the kernel's resident CTAs, so that the last wave is
-// not left mostly idle.  It depends only on the instance's sizes and the device's resident-CTA
-// count, never on what else runs in the same launch.
-int canonical_splits(int64_t np, int64_t nq, int R, int resident) {
+// Micro-splits of one sweep of an instance: enough runs of the reduced side that any launch can
+// cut the instance into balanced work items (about 65536 point-block runs), each run at least 4
+// tiles and an even number of tiles (a pipeline stage never straddles two runs), at most 64 runs.
+// The layout depends only on the instance's sizes and the plan's R, so the instance's partials,
+// and hence its results, are the same in every launch that contains it.
+void micro_splits(int64_t np, int64_t nq, int R, int* nms, int* mst) {
   const int pblks = (int)((np + kThreads * R - 1) / (kThreads * R));
   const int qtiles = (int)((nq + kTQ - 1) / kTQ);
-  int best = 1;
-  double best_eff = -1.0;
-  const int smax = std::max(1, std::min(kMaxSplits, qtiles / kMinSplitTiles));
-  for (int s = 1; s <= smax; ++s) {
-    const int tps = (qtiles + s - 1) / s;
-    const int sp = (qtiles + tps - 1) / tps;  // no empty split
-    if (sp != s) continue;
-    const double waves = (double)pblks * sp / resident;
+  int n = std::max(1, std::min({(65536 + pblks - 1) / pblks, kMaxSplits, qtiles / kMinSplitTiles}));
+  int t = (qtiles + n - 1) / n;
+  if (n > 1 && (t & 1)) ++t;
+  n = (qtiles + t - 1) / t;
+  *nms = n;
+  *mst = n > 1 ? t : qtiles;
+}
+
+// Micro-splits per work item for an instance that runs alone: the largest grouping whose items
+// (all about the same size) fill close to a whole number of waves of the resident CTAs.
+int solo_group(int pblks, int nms, int resident) {
+  int best = nms, last_per = -1;
+  double best_eff = -1.0, best_waves = 0.0;
+  for (int g = nms; g >= 1; --g) {
+    const int per = (nms + g - 1) / g;  // items per point block
+    if (per == last_per) continue;       // a larger grouping already gave this item count
+    last_per = per;
+    const double waves = (double)pblks * per / resident;
     const double eff = waves / std::ceil(waves);
-    if (eff >= 0.95 && waves >= 1.0) return sp;
-    if (eff > best_eff + 1e-9) {
-      best_eff = eff;
-      best = sp;
+    if (eff >= 0.95 && waves >= 2.0) return g;
+    if (eff > best_eff + 0.01 || (eff > best_eff - 0.01 && waves > best_waves)) {
+      best_eff = std::max(eff, best_eff);
+      best_waves = waves;
+      best = g;
     }
   }
   return best;
@@ -127,18 +137,21 @@ void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl) {
   pl.pblk_col = (int)((in.m + rpb - 1) / rpb);
   SweepFn fn = get_sweep(in.d, mode, R, ch, 0);
   const int resident = ctx.resident_ctas(fn);
-  pl.splits_row = canonical_splits(in.n, in.m, R, resident);
-  pl.splits_col = canonical_splits(in.m, in.n, R, resident);
-  pl.n_row = pl.pblk_row * pl.splits_row;
-  pl.n_col = pl.pblk_col * pl.splits_col;
+  micro_splits(in.n, in.m, R, &pl.nms_row, &pl.mst_row);
+  micro_splits(in.m, in.n, R, &pl.nms_col, &pl.mst_col);
+  pl.group_row = solo_group(pl.pblk_row, pl.nms_row, resident);
+  pl.group_col = solo_group(pl.pblk_col, pl.nms_col, resident);
+  pl.n_row = pl.pblk_row * ((pl.nms_row + pl.group_row - 1) / pl.group_row);
+  pl.n_col = pl.pblk_col * ((pl.nms_col + pl.group_col - 1) / pl.group_col);
   pl.grid_row = std::min(pl.n_row, resident);
   pl.grid_col = std::min(pl.n_col, resident);
 }
 
-static void build_items(std::vector<Item>& out, int inst, int pblks, int splits) {
-  // split-major order: the CTAs of one wave cover many point blocks of the same splits
-  for (int s = 0; s < splits; ++s)
-    for (int b = 0; b < pblks; ++b) out.push_back(Item{inst, b, s, splits});
+// Work items of one sweep of one instance: every point block times runs of `group` consecutive
+// micro-splits (the last run may be shorter).
+void build_items(std::vector<Item>& out, int inst, int pblks, int nms, int group) {
+  for (int m0 = 0; m0 < nms; m0 += group)
+    for (int b = 0; b < pblks; ++b) out.push_back(Item{inst, b, m0, std::min(group, nms - m0)});
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -229,6 +242,15 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   h.tiles_x = (int)((in.n + kTQ - 1) / kTQ);
   h.tiles_y = (int)((in.m + kTQ - 1) / kTQ);
   h.pblk_x = in.cert.pblk_row;
+  {
+    const LaunchPlan* pls[2] = {&in.fast, &in.cert};
+    for (int q = 0; q < 2; ++q) {
+      h.nms[q][0] = pls[q]->nms_row;
+      h.nms[q][1] = pls[q]->nms_col;
+      h.ms_tiles[q][0] = pls[q]->mst_row;
+      h.ms_tiles[q][1] = pls[q]->mst_col;
+    }
+  }
   h.n = (int)in.n;
   h.m = (int)in.m;
   h.d = in.d;
@@ -238,7 +260,7 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   const size_t n = in.n, m = in.m;
   size_t nsp = 0;
   for (const LaunchPlan* pl : {&in.fast, &in.cert})
-    nsp = std::max(nsp, std::max((size_t)pl->splits_row * n, (size_t)pl->splits_col * m));
+    nsp = std::max(nsp, std::max((size_t)pl->nms_row * n, (size_t)pl->nms_col * m));
   const size_t maxblk = (std::max(n, m) + kThreads - 1) / kThreads;
   Layout& L = in.layout;
   Carve cv;
@@ -374,8 +396,8 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
 
   std::vector<Item> items;
   for (const LaunchPlan* pl : {&in.fast, &in.cert}) {
-    build_items(items, 0, pl->pblk_row, pl->splits_row);
-    build_items(items, 0, pl->pblk_col, pl->splits_col);
+    build_items(items, 0, pl->pblk_row, pl->nms_row, pl->group_row);
+    build_items(items, 0, pl->pblk_col, pl->nms_col, pl->group_col);
   }
   OT_CUDA(cudaMemcpyAsync(items_base, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, s));
   OT_CUDA(cudaMemcpyAsync(in.d_inst, &h, sizeof(Inst), cudaMemcpyHostToDevice, s));

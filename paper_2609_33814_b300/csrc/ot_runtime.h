@@ -41,7 +41,9 @@ struct LaunchPlan {
   int mode = 0;
   int R = 1, ch = 16;
   int pblk_row = 0, pblk_col = 0;
-  int splits_row = 1, splits_col = 1;
+  int nms_row = 1, nms_col = 1;      // micro-splits of the reduced side (fixed per instance)
+  int mst_row = 1, mst_col = 1;      // tiles per micro-split
+  int group_row = 1, group_col = 1;  // micro-splits per work item when the instance runs alone
   Item* d_row = nullptr;
   Item* d_col = nullptr;
   int n_row = 0, n_col = 0;
@@ -95,6 +97,7 @@ struct Instance {
 ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q);
 void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl);
 void canonical_tile(int d, int mode, int* R, int* ch);
+void build_items(std::vector<Item>& out, int inst, int pblks, int nms, int group);
 ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
 ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
 ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p);

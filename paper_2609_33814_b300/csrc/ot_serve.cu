@@ -199,23 +199,34 @@ void Server::run_chunk(Lane& L) {
       const bool row = kind % 2 == 0;
       SweepFn fn = get_sweep(L.d, mode_of[kind], R, kind < 2 ? L.ch_fast : 8, 0);
       const int resident = ctx.resident_ctas(fn);
-      // each instance contributes its own work items (its plan fixes its numerics)
+      // Each instance's micro-split layout is fixed (its numerics do not depend on the batch);
+      // the launch groups micro-splits into items of about equal size for this composition:
+      // roughly four waves of resident CTAs in total.
+      double tiles_total = 0;
+      for (size_t i = 0; i < na; ++i) {
+        const Instance& in = *L.active[i]->inst;
+        const LaunchPlan& pl = kind < 2 ? in.fast : in.cert;
+        const int64_t nq = row ? in.m : in.n;
+        tiles_total += (double)(row ? pl.pblk_row : pl.pblk_col) * (double)((nq + kTQ - 1) / kTQ);
+      }
+      const double target = std::max(1.0, tiles_total / (4.0 * resident));
       L.off[kind] = (int)items.size();
       for (size_t i = 0; i < na; ++i) {
         const Instance& in = *L.active[i]->inst;
         const LaunchPlan& pl = kind < 2 ? in.fast : in.cert;
-        const int pblks = row ? pl.pblk_row : pl.pblk_col;
-        const int splits = row ? pl.splits_row : pl.splits_col;
-        for (int sp = 0; sp < splits; ++sp)
-          for (int b = 0; b < pblks; ++b) items.push_back(Item{(int)i, b, sp, splits});
+        const int nms = row ? pl.nms_row : pl.nms_col;
+        const int mst = row ? pl.mst_row : pl.mst_col;
+        const int group = std::max(1, std::min(nms, (int)std::lround(target / mst)));
+        build_items(items, (int)i, row ? pl.pblk_row : pl.pblk_col, nms, group);
       }
       // longest items first: CTAs take items with a fixed stride, so this evens out their loads
       auto work_of = [&](const Item& it) {
         const Instance& in = *L.active[it.inst]->inst;
+        const LaunchPlan& pl = kind < 2 ? in.fast : in.cert;
         const int64_t nq = row ? in.m : in.n;
         const int qtiles = (int)((nq + kTQ - 1) / kTQ);
-        const int tps = (qtiles + it.nsplit - 1) / it.nsplit;
-        return std::min(tps, qtiles - it.split * tps);
+        const int mst = row ? pl.mst_row : pl.mst_col;
+        return std::min(qtiles, (it.ms0 + it.nms) * mst) - it.ms0 * mst;
       };
       std::stable_sort(items.begin() + L.off[kind], items.end(),
                        [&](const Item& a, const Item& b) { return work_of(a) > work_of(b); });

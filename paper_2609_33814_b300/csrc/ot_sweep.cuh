@@ -122,8 +122,15 @@ struct Acc<R, kSweepF64> {
 //   CERT   column sweep also accumulates N_q = sum_p ||u-w||^2 E_pq (Algorithm 2)
 //   UPDATE false: standalone certificate of the current state, no state update
 // ---------------------------------------------------------------------------------------------
+// Fast sweeps keep five CTAs resident per SM (<= 102 registers) when R x D <= 4 and three
+// (<= 170) when R x D <= 12; the rarely run epilogue may spill rather than the hot loop lose warps.
+template <int D, int R, int MODE>
+constexpr int sweep_min_blocks() {
+  return MODE != kSweepFast ? 1 : (R * D <= 4 ? 5 : (R * D <= 12 ? 3 : 1));
+}
+
 template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict__ insts,
+__global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) sweep_kernel(const Inst* __restrict__ insts,
                                                          const Item* __restrict__ items, int nitems) {
   static_assert(!(CERT && MODE == kSweepFast), "certificate sweeps use the compensated or FP64 mode");
   static_assert(UPDATE || (CERT && SIDE == 1), "a non-updating sweep is the standalone certificate");
@@ -158,9 +165,9 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
     const Item itp = items[pr_it];
     const Inst* Ip = insts + itp.inst;
     const int qtl = SIDE == 0 ? Ip->tiles_y : Ip->tiles_x;
-    const int tpsp = (qtl + itp.nsplit - 1) / itp.nsplit;
-    pr_qt0 = itp.split * tpsp;
-    pr_ntl = min(qtl, pr_qt0 + tpsp) - pr_qt0;
+    const int mstp = Ip->ms_tiles[CERT ? 1 : 0][SIDE];
+    pr_qt0 = itp.ms0 * mstp;
+    pr_ntl = min(qtl, (itp.ms0 + itp.nms) * mstp) - pr_qt0;
     pr_nst = (pr_ntl + kStageTiles - 1) / kStageTiles;
     pr_qpack = SIDE == 0 ? Ip->ypack : Ip->xpack;
     pr_us = 0;
@@ -188,12 +195,12 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
     const Inst* __restrict__ I = insts + item.inst;
     const int np = SIDE == 0 ? I->n : I->m;
     const int qtiles = SIDE == 0 ? I->tiles_y : I->tiles_x;
-    const int splits = item.nsplit;
+    const int splits = I->nms[CERT ? 1 : 0][SIDE];      // partials per point (all micro-splits)
+    const int mst = I->ms_tiles[CERT ? 1 : 0][SIDE];    // tiles per micro-split
     const int pblks = (np + kThreads * R - 1) / (kThreads * R);
     const float* __restrict__ ppack = SIDE == 0 ? I->xpack : I->ypack;
-    const int tps = (qtiles + splits - 1) / splits;
-    const int qt0 = item.split * tps;
-    const int qt1 = min(qtiles, qt0 + tps);
+    const int qt0 = item.ms0 * mst;
+    const int qt1 = min(qtiles, (item.ms0 + item.nms) * mst);
     const int ntl = qt1 - qt0;
     const long long kiter = *I->k - (UPDATE ? 0 : 1);
     const double eps = eps_of(I, kiter);
@@ -218,22 +225,41 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
       }
     }
     Acc<R, MODE> st;
+    auto reset = [&]() {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      st.mref[r] = 0;
-      st.s[r] = 0;
-      if constexpr (MODE != kSweepF64) {
-        st.kc[r] = 0.0f;
-        st.n[r] = 0.0f;
-        st.nc[r] = 0.0f;
-      } else {
-        st.n[r] = 0.0;
+      for (int r = 0; r < R; ++r) {
+        st.mref[r] = 0;
+        st.s[r] = 0;
+        if constexpr (MODE != kSweepF64) {
+          st.kc[r] = 0.0f;
+          st.n[r] = 0.0f;
+          st.nc[r] = 0.0f;
+        } else {
+          st.n[r] = 0.0;
+        }
+        if constexpr (MODE == kSweepFast) {
+          st.acc[r] = 0ull;
+          st.M2[r] = 0ull;
+        }
       }
-      if constexpr (MODE == kSweepFast) {
-        st.acc[r] = 0ull;
-        st.M2[r] = 0ull;
+    };
+    reset();
+    Part* part = reinterpret_cast<Part*>(I->part);
+    // one split partial per micro-split: (shift, sum[, cost-weighted sum]) per point
+    auto write_partial = [&](int ms) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+        if (p < np) {
+          Part pr;
+          pr.x = st.mref[r];
+          pr.y = st.s[r];
+          pr.z = st.n[r];
+          pr.w = 0;
+          part[(size_t)ms * np + p] = pr;
+        }
       }
-    }
+    };
     u64 A2[R][D];
     if constexpr (MODE == kSweepFast) {
 #pragma unroll
@@ -245,6 +271,7 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
     const int nst = (ntl + kStageTiles - 1) / kStageTiles;  // pipeline stages of this item
 
     bool fresh = true;
+    int tiles_done = 0, ms_cur = item.ms0, ms_end = min(ntl, mst);  // micro-split bookkeeping
     for (int us = 0; us < nst; ++us) {
       const uint32_t g = gcons + us;
       const int stg = g % kStages;
@@ -498,6 +525,13 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
         }
       }
 
+        // end of a micro-split: publish its partial and start the next one afresh
+        if (++tiles_done == ms_end) {
+          write_partial(ms_cur++);
+          reset();
+          fresh = true;
+          ms_end = min(ntl, ms_end + mst);
+        }
       }  // tiles of the stage
 
       const int all_ok = __syncthreads_and(ok ? 1 : 0);
@@ -514,25 +548,11 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
     }
     gcons += nst;
 
-    // ---- write this split's partials ----
-    Part* part = reinterpret_cast<Part*>(I->part);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
-      if (p < np) {
-        Part pr;
-        pr.x = st.mref[r];
-        pr.y = st.s[r];
-        pr.z = st.n[r];
-        pr.w = 0;
-        part[(size_t)item.split * np + p] = pr;
-      }
-    }
-
     // ---- last CTA of this point block runs the epilogue ----
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_flag = (atomicAdd(&I->cnt[item.pblk], 1u) == (unsigned)(splits - 1));
+    if (tid == 0)
+      s_flag = (atomicAdd(&I->cnt[item.pblk], (unsigned)item.nms) + (unsigned)item.nms == (unsigned)splits);
     __syncthreads();
     if (!s_flag) continue;
     __threadfence();
@@ -547,35 +567,72 @@ __global__ void __launch_bounds__(kThreads) sweep_kernel(const Inst* __restrict_
       const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
       if (p >= np) continue;
       // merge the splits in index order: a fixed order keeps the result deterministic
-      double mx = -INFINITY, S = 0.0, N = 0.0;
-      for (int s0 = 0; s0 < splits; s0 += 8) {
-        Part pr[8];
+      double mx, S, N;
+      if constexpr (MODE == kSweepF64) {
+        mx = -INFINITY;
+        S = 0.0;
+        N = 0.0;
+        for (int s0 = 0; s0 < splits; s0 += 8) {
+          Part pr[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (s0 + u < splits) pr[u] = load_part(&part[(size_t)(s0 + u) * np + p]);
+          for (int u = 0; u < 8; ++u)
+            if (s0 + u < splits) pr[u] = load_part(&part[(size_t)(s0 + u) * np + p]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (s0 + u >= splits) break;
-          const double ms = (double)pr[u].x;  // integer-valued shifts: rescaling is exact
-          if (ms > mx) {
-            const double f = pow2i(mx - ms);
-            S = S * f + (double)pr[u].y;
-            N = N * f + (double)pr[u].z;
-            mx = ms;
-          } else {
-            const double f = pow2i(ms - mx);
-            S += (double)pr[u].y * f;
-            N += (double)pr[u].z * f;
+          for (int u = 0; u < 8; ++u) {
+            if (s0 + u >= splits) break;
+            const double ms = (double)pr[u].x;  // integer-valued shifts: rescaling is exact
+            if (ms > mx) {
+              const double f = pow2i(mx - ms);
+              S = S * f + (double)pr[u].y;
+              N = N * f + (double)pr[u].z;
+              mx = ms;
+            } else {
+              const double f = pow2i(ms - mx);
+              S += (double)pr[u].y * f;
+              N += (double)pr[u].z * f;
+            }
           }
         }
+      } else {
+        // FP32 partials merged in FP32: exact power-of-two rescaling and Kahan sums (B300's FP64
+        // pipe is slow, and an instance can have tens of split partials per point)
+        float mxf = -INFINITY, Sf = 0.0f, Sc = 0.0f, Nf = 0.0f, Nc = 0.0f;
+        for (int s0 = 0; s0 < splits; s0 += 4) {
+          Part pr[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (s0 + u < splits) pr[u] = load_part(&part[(size_t)(s0 + u) * np + p]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (s0 + u >= splits) break;
+            const float ms = pr[u].x;
+            if (s0 + u == 0) {
+              mxf = ms;
+              Sf = pr[u].y;
+              Nf = pr[u].z;
+            } else if (ms > mxf) {
+              const float f = exp2_neg_int(ms - mxf);
+              Sf *= f;
+              Sc *= f;
+              Nf *= f;
+              Nc *= f;
+              mxf = ms;
+              kahan_add(Sf, Sc, pr[u].y);
+              if constexpr (ACCN) kahan_add(Nf, Nc, pr[u].z);
+            } else {
+              const float f = exp2_neg_int(mxf - ms);
+              kahan_add(Sf, Sc, pr[u].y * f);
+              if constexpr (ACCN) kahan_add(Nf, Nc, pr[u].z * f);
+            }
+          }
+        }
+        mx = (double)mxf;
+        S = (double)Sf - (double)Sc;
+        N = (double)Nf - (double)Nc;
       }
       double lse2;
       if constexpr (MODE == kSweepFast) {
-        // log2 S = exponent + log2(mantissa): the FP32 sweep's own rounding (~1e-7) dominates the
-        // FP32 log2 of the mantissa, and B300's FP64 pipe is slow
-        int ex;
-        const double mant = frexp(S, &ex);
-        lse2 = mx + (double)ex + (double)__log2f((float)mant);
+        lse2 = mx + (double)__log2f((float)S);  // FP32 log2 is below the FP32 sweep's own rounding
       } else {
         lse2 = mx + log2(S);
       }

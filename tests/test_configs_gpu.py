@@ -1,0 +1,92 @@
+"""Parity at the benchmark configurations' sizes, where the dense oracle cannot run a whole solve.
+
+* 32x32 grid, FP64, eps0 = 1, lambda = 1, 2000 iterations, certificate every 100: the oracle
+  re-evaluates the certificate (Prop. 3, Algorithm 2) from the final GPU state, and takes one
+  iteration of Algorithm 1 from it, for comparison with the GPU's next iteration.
+* A batch of 8 uneven O-BDRS instances (5 x 256^2 and 3 x 512^2 grids) in one server lane:
+  sampled rows of the first iteration's potentials against the oracle's on-the-fly LSE.
+* The large colour-transfer size (n = m = 10,022,870, d = 3): sampled rows of the first row sweep.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import ot_inputs as I
+
+pytestmark = pytest.mark.gpu
+P = pytest.importorskip("paper_2609_33814_b300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return P.Context(0)
+
+
+def test_grid32_fp64_2000_iterations(ctx):
+    prob = I.grid_problem(32, seed=2609)
+    S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0, lam=1.0,
+                  precision="fp64", cert_every=100)
+    res = S.step(2000)
+    assert res["iters"] == 2000 and res["n_certs"] == 20
+    assert res["L_best"] <= res["U_best"]
+    # the oracle's certificate of the GPU state after iteration 1999 (a certificate iteration)
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    lah, lbh, lbt = S.get(P.OT_LOG_ALPHA_HAT), S.get(P.OT_LOG_BETA_HAT), S.get(P.OT_LOG_BETA_TILDE)
+    eps = O.eps_schedule(1.0, 1.0, 1999)
+    cert = O.certificate(lah, lbh, lbt, prob.a, prob.b, C, eps, prob.omega)
+    assert abs(cert["U"] - res["U"]) <= 1e-6 and abs(cert["L"] - res["L"]) <= 1e-6, (cert["U"], res["U"])
+    # one more iteration from that state on both sides
+    st = O.DualState(S.get(P.OT_LOG_ALPHA), S.get(P.OT_LOG_BETA), S.get(P.OT_LOG_BETA_PREV), lah, lbh, lbt,
+                     2000, eps)
+    st1 = O.dual_obdrs_step(st, np.log(prob.a), np.log(prob.b), C, 1.0, 1.0)
+    S.step(1)
+    f_g = st1.eps * S.get(P.OT_LOG_ALPHA_HAT)
+    f_o = st1.eps * st1.log_alpha_hat
+    g_g = st1.eps * (S.get(P.OT_LOG_BETA_HAT) - np.log(prob.b))
+    g_o = st1.eps * (st1.log_beta_hat - np.log(prob.b))
+    scale = max(np.abs(f_o).max(), np.abs(g_o).max())
+    assert max(np.abs(f_g - f_o).max(), np.abs(g_g - g_o).max()) / scale <= 1e-9
+    S.close()
+
+
+def test_batch_of_eight_uneven_obdrs_instances(ctx):
+    import torch
+    sizes = [256, 256, 512, 256, 512, 256, 512, 256]
+    classes = ["uniform", "gaussmix", "cauchy", "sparse"]
+    probs = [I.grid_problem(s, 100 + i, classes[i % 4], classes[(i + 1) % 4]) for i, s in enumerate(sizes)]
+    lams = [1.5 if i % 2 else 1.99 for i in range(8)]
+    srv = P.Server(ctx, hbm_budget_bytes=32 << 30, max_slots=8)
+    ids = []
+    for p, lam in zip(probs, lams):
+        dev = [torch.from_numpy(v).cuda() for v in (p.x, p.y, p.a, p.b)]
+        ids.append(srv.submit(*dev, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15, eps0=1.0, lam=lam,
+                              max_iters=1, cert_every=1, precision="mufu"))
+    rng = np.random.default_rng(1)
+    for rid, p, lam in zip(ids, probs, lams):
+        f, g, res = srv.wait(rid, 300.0)
+        assert res["iters"] == 1 and res["L"] <= res["U"]
+        a = np.maximum(p.a, 1e-15)
+        a = a / a.sum()
+        rows = np.sort(rng.choice(p.n, size=16, replace=False))
+        lse = O.row_lse_sampled(rows, p.x, p.y, np.zeros(p.m), p.kappa, 1.0)  # k = 0: eps = eta, beta-tilde = 1
+        f_o = 1.0 * (np.log(a[rows]) - lse)
+        assert np.abs(f[rows] - f_o).max() / np.abs(f_o).max() <= 1e-6, p.name
+    srv.close()
+
+
+def test_large_colour_transfer_size_sampled_rows(ctx):
+    import torch
+    n = 4238 * 2365
+    prob = I.rgb_problem(n, seed=5)
+    eta = 0.01
+    dev = [torch.from_numpy(v).cuda() for v in (prob.x, prob.y, prob.a, prob.b)]
+    S = ctx.state(*dev, cost_scale=prob.kappa, omega=1.0, eps0=eta, cert_every=0)
+    del dev
+    S.step(1)
+    lah = S.get(P.OT_LOG_ALPHA_HAT)
+    rows = np.sort(np.random.default_rng(3).choice(n, size=6, replace=False))
+    lse = O.row_lse_sampled(rows, prob.x, prob.y, np.zeros(n), prob.kappa, eta, chunk=1 << 20)
+    ref = np.log(prob.a[rows]) - lse
+    err = np.abs(eta * (lah[rows] - ref)).max() / np.abs(eta * ref).max()
+    assert err <= 1e-5, err
+    S.close()
