@@ -120,6 +120,18 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------------------------
+def combine_over_ranks(td, device, t_step, entries, e2e_t, e2e_entries):
+    """Whole-job numbers from per-rank ones: the slowest rank's time, the sum of the work.
+
+    Every rank serves its own stream (independent replicas), so the only exchange is this one."""
+    import torch
+    tt = torch.tensor([t_step, entries, e2e_t, e2e_entries], dtype=torch.float64, device=device)
+    gathered = [torch.zeros_like(tt) for _ in range(td.get_world_size())]
+    td.all_gather(gathered, tt)
+    return (max(float(g[0]) for g in gathered), sum(float(g[1]) for g in gathered),
+            max(float(g[2]) for g in gathered), sum(float(g[3]) for g in gathered))
+
+
 def make_stream(args, rank: int):
     reqs = I.serving_stream(args.requests, args.seed + 7919 * rank, args.rate)
     if args.burst:
@@ -381,14 +393,8 @@ def run_ours(args, rank: int, world: int):
     t_step = max(step_times)
     entries = sum(r["entries"] for r in results) / len(results)
     if dist:
-        tt = torch.tensor([t_step, entries, statistics.median(e2e_times), e2e_res[-1]["entries"]],
-                          dtype=torch.float64, device="cuda")
-        gathered = [torch.zeros_like(tt) for _ in range(world)]
-        td.all_gather(gathered, tt)
-        t_step = max(float(g[0]) for g in gathered)
-        entries_all = sum(float(g[1]) for g in gathered)
-        e2e_t = max(float(g[2]) for g in gathered)
-        e2e_entries = sum(float(g[3]) for g in gathered)
+        t_step, entries_all, e2e_t, e2e_entries = combine_over_ranks(
+            td, "cuda", t_step, entries, statistics.median(e2e_times), e2e_res[-1]["entries"])
     else:
         entries_all = entries
         e2e_t = statistics.median(e2e_times)

@@ -49,8 +49,8 @@ typedef enum {
  * (float-float exponent) sweeps in the FP32 modes and FP64 sweeps in OT_FP64. */
 typedef enum {
   OT_EXP_MUFU = 0,    /* FP32 exponent, MUFU exp2, FP64 potentials (the fast path) */
-  OT_EXP_POLY = 1,    /* FP32 exponent, exp2 by an FMA-pipe polynomial */
-  OT_EXP_SPLIT = 2,   /* FP32 exponent, exp2 split between MUFU and the polynomial */
+  OT_EXP_POLY = 1,    /* FP32 exponent, exp2 by an FMA-pipe polynomial (max rel. error 5e-7) */
+  OT_EXP_SPLIT = 2,   /* FP32 exponent, exp2 for a quarter of the entries by the polynomial */
   OT_FP64 = 3,        /* FP64 exponent, exp2 and sums */
   OT_FP32_COMP = 4    /* compensated float-float exponent on every iteration */
 } ot_precision;
@@ -254,6 +254,13 @@ ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, const float* x,
 ot_status ot_profile_enable(ot_context* ctx, int on);
 ot_status ot_profile_reset(ot_context* ctx);
 ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* entries, double* ms);
+
+/* Failure-injection support (tests): the number of times a sweep polls a tile's arrival before it
+ * gives up, records the error and returns (the state then reports OT_ETIMEDOUT and must be
+ * destroyed).  Applies to states created on this context afterwards; 0 makes every wait give up at
+ * once.  The copies already in flight are still waited for, with the normal bound, before a sweep
+ * returns.  The default is 2^26 polls (seconds). */
+ot_status ot_debug_set_wait_limit(ot_context* ctx, uint32_t polls);
 
 /* Number of CUDA kernels this context has launched since creation or the last ot_profile_reset
  * (every node of a replayed CUDA graph counts). */

@@ -107,6 +107,7 @@ _lib.ot_profile_enable.argtypes = [_P, C.c_int]
 _lib.ot_profile_reset.argtypes = [_P]
 _lib.ot_profile_read.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
 _lib.ot_launch_count.argtypes = [_P, C.POINTER(C.c_int64)]
+_lib.ot_debug_set_wait_limit.argtypes = [_P, C.c_uint32]
 _lib.ot_probe_pipes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int]
 
 

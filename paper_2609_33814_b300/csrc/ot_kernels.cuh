@@ -15,11 +15,13 @@ constexpr uint32_t kWaitLimit = 1u << 26;  // mbarrier polls before a sweep give
 // Error bits written to Inst::err by device code.
 enum : int { kErrTimeout = 1, kErrNonFinite = 2 };
 
-// Exp2 implementations of the FP32 sweep.
-enum : int { kExpMufu = 0, kExpPoly = 1, kExpSplit = 2 };
+// Precision of one sweep launch.  The three fast modes differ only in how exp2 is evaluated:
+// MUFU, an FMA-pipe polynomial, or a fixed split between the two.
+enum : int { kSweepFast = 0, kSweepComp = 1, kSweepF64 = 2, kSweepFastPoly = 3, kSweepFastSplit = 4 };
 
-// Precision of one sweep launch.
-enum : int { kSweepFast = 0, kSweepComp = 1, kSweepF64 = 2 };
+__host__ __device__ constexpr bool is_fast_mode(int mode) {
+  return mode == kSweepFast || mode == kSweepFastPoly || mode == kSweepFastSplit;
+}
 
 // Certificate record layout (doubles) written by the last CTA of a certificate iteration.
 enum : int {
@@ -42,6 +44,7 @@ struct Inst {
   // results do not depend on how a launch groups micro-splits into work items.
   int nms[2][2];
   int ms_tiles[2][2];
+  uint32_t wait_limit;           // mbarrier polls before a sweep gives up waiting for a tile
   double kappa, eta, lambda, omega;
   float* xpack;                  // [tiles_x][kNComp][kTQ]
   float* ypack;                  // [tiles_y][kNComp][kTQ]

@@ -176,9 +176,11 @@ struct Carve {
     }                                                                                 \
   } while (0)
 
-static int sweep_mode_of(int precision) {
+int sweep_mode_of(int precision) {
   if (precision == OT_FP64) return kSweepF64;
   if (precision == OT_FP32_COMP) return kSweepComp;
+  if (precision == OT_EXP_POLY) return kSweepFastPoly;
+  if (precision == OT_EXP_SPLIT) return kSweepFastSplit;
   return kSweepFast;
 }
 
@@ -216,8 +218,9 @@ ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q) {
     ctx.set_error("max_iters and cert_every must be >= 0");
     return OT_EINVAL;
   }
-  if (q->precision != OT_EXP_MUFU && q->precision != OT_FP64 && q->precision != OT_FP32_COMP) {
-    ctx.set_error("precision %d is not available", q->precision);
+  if (q->precision != OT_EXP_MUFU && q->precision != OT_FP64 && q->precision != OT_FP32_COMP &&
+      q->precision != OT_EXP_POLY && q->precision != OT_EXP_SPLIT) {
+    ctx.set_error("unknown precision %d", q->precision);
     return OT_EINVAL;
   }
   return OT_OK;
@@ -235,13 +238,13 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   in.stream = stream;
   in.sweep_mode = sweep_mode_of(q->precision);
   in.cert_mode = q->precision == OT_FP64 ? kSweepF64 : kSweepComp;
-  in.exp_mode = q->precision == OT_EXP_POLY ? kExpPoly : (q->precision == OT_EXP_SPLIT ? kExpSplit : kExpMufu);
   plan_launch(ctx, in, in.sweep_mode, in.fast);
   plan_launch(ctx, in, in.cert_mode, in.cert);
   Inst& h = in.h;
   h.tiles_x = (int)((in.n + kTQ - 1) / kTQ);
   h.tiles_y = (int)((in.m + kTQ - 1) / kTQ);
   h.pblk_x = in.cert.pblk_row;
+  h.wait_limit = ctx.wait_limit;
   {
     const LaunchPlan* pls[2] = {&in.fast, &in.cert};
     for (int q = 0; q < 2; ++q) {
@@ -829,6 +832,12 @@ ot_status ot_profile_reset(ot_context* ctx) {
   if (!ctx) return OT_EINVAL;
   for (auto& s : ctx->c.stats) s = KernelStats();
   ctx->c.launches = 0;
+  return OT_OK;
+}
+
+ot_status ot_debug_set_wait_limit(ot_context* ctx, uint32_t polls) {
+  if (!ctx) return OT_EINVAL;
+  ctx->c.wait_limit = polls;
   return OT_OK;
 }
 

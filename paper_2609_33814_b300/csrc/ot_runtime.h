@@ -26,6 +26,7 @@ struct Context {
   bool profile = false;
   KernelStats stats[4];  // fast row, fast column, certificate row, certificate column
   int64_t launches = 0;  // every kernel this context has launched (graph nodes included)
+  uint32_t wait_limit = kWaitLimit;  // tile-wait bound given to the states created from now on
   int sms = 148;
   int cc_major = 0, cc_minor = 0;
   cudaStream_t stream = nullptr;
@@ -74,7 +75,7 @@ struct Instance {
   ot_params params{};
   int64_t n = 0, m = 0;
   int d = 0;
-  int sweep_mode = 0, cert_mode = 1, exp_mode = 0;
+  int sweep_mode = 0, cert_mode = 1;
   bool use_graphs = true;
   // used by the batched server: stream-ordered allocation and a shared pinned read-back slot
   bool async_alloc = false;
@@ -97,6 +98,7 @@ struct Instance {
 ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q);
 void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl);
 void canonical_tile(int d, int mode, int* R, int* ch);
+int sweep_mode_of(int precision);
 void build_items(std::vector<Item>& out, int inst, int pblks, int nms, int group);
 ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
 ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);

@@ -104,9 +104,7 @@ struct Server {
 static const int kMaxLaunch = 4;  // fast row, fast col, cert row, cert col
 
 int Server::lane_for(const Request* r) {
-  const int mode = r->params.precision == OT_FP64 ? kSweepF64
-                   : r->params.precision == OT_FP32_COMP ? kSweepComp
-                                                         : kSweepFast;
+  const int mode = sweep_mode_of(r->params.precision);
   for (int i = 0; i < nlanes; ++i) {
     const Lane& L = lanes[i];
     if (L.d == r->prob.d && L.mode == mode && L.ce == r->params.cert_every) return i;
@@ -514,7 +512,6 @@ ot_status ot_serve_submit(ot_server* sv, const ot_problem* prob, const ot_params
   if (!sv || !prob || !params || !req_id) return OT_EINVAL;
   Server& S = sv->s;
   if (params->cert_every < 1) return OT_EINVAL;
-  if (params->precision == OT_EXP_POLY || params->precision == OT_EXP_SPLIT) return OT_EINVAL;
   Request* r = new (std::nothrow) Request();
   if (!r) return OT_ENOMEM;
   r->params = *params;

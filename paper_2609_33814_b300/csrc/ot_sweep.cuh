@@ -25,6 +25,7 @@
 #include <type_traits>
 
 #include "ot_device.cuh"
+#include "ot_exp2_poly.cuh"
 #include "ot_kernels.cuh"
 
 namespace ot {
@@ -42,6 +43,31 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   const float t = __fadd_rn(s, y);
   c = __fsub_rn(__fsub_rn(t, s), y);
   s = t;
+}
+
+// 2^x for a pair, on the FP32/INT pipes: x = n + f with n = round(x) (magic-number rounding),
+// 2^f by the fitted polynomial (|f| <= 1/2), 2^n added into the exponent bits.  x is clamped to
+// [-125, 126] so the result stays a normal float (an overflow still shows up as a huge value).
+__device__ __forceinline__ u64 exp2_poly2(u64 v) {
+  float lo, hi;
+  up2(v, lo, hi);
+  lo = fminf(fmaxf(lo, -125.0f), 126.0f);
+  hi = fminf(fmaxf(hi, -125.0f), 126.0f);
+  const u64 x = pk2(lo, hi);
+  const u64 magic = pk2(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+  const u64 t = add2(x, magic);
+  const u64 f = sub2(x, sub2(t, magic));
+  u64 p = fma2(pk2(kExp2Poly[5], kExp2Poly[5]), f, pk2(kExp2Poly[4], kExp2Poly[4]));
+  p = fma2(p, f, pk2(kExp2Poly[3], kExp2Poly[3]));
+  p = fma2(p, f, pk2(kExp2Poly[2], kExp2Poly[2]));
+  p = fma2(p, f, pk2(kExp2Poly[1], kExp2Poly[1]));
+  p = fma2(p, f, pk2(kExp2Poly[0], kExp2Poly[0]));
+  float t0, t1, p0, p1;
+  up2(t, t0, t1);
+  up2(p, p0, p1);
+  p0 = __int_as_float(__float_as_int(p0) + (__float_as_int(t0) << 23));
+  p1 = __int_as_float(__float_as_int(p1) + (__float_as_int(t1) << 23));
+  return pk2(p0, p1);
 }
 
 __device__ __forceinline__ size_t pack_idx(int p, int comp) {
@@ -96,26 +122,28 @@ __device__ __forceinline__ PartF64 load_part(const PartF64* p) {
 // ---------------------------------------------------------------------------------------------
 // Per-thread accumulator state for R thread-side points.
 // ---------------------------------------------------------------------------------------------
-template <int R, int MODE>
+template <int R, int MODE, bool FAST = is_fast_mode(MODE)>
 struct Acc;
 
-template <int R>
-struct Acc<R, kSweepFast> {
+template <int R, int MODE>
+struct Acc<R, MODE, true> {
   float mref[R], s[R], kc[R], n[R], nc[R];
   u64 acc[R], M2[R];
 };
 template <int R>
-struct Acc<R, kSweepComp> {
+struct Acc<R, kSweepComp, false> {
   float mref[R], s[R], kc[R], n[R], nc[R];
 };
 template <int R>
-struct Acc<R, kSweepF64> {
+struct Acc<R, kSweepF64, false> {
   double mref[R], s[R], n[R];
 };
 
 // ---------------------------------------------------------------------------------------------
 // The sweep kernel.
 //   MODE   kSweepFast: FP32 exponent, f32x2 FMAs, MUFU exp2 (the hot path)
+//          kSweepFastPoly / kSweepFastSplit: the same with exp2 by the FMA-pipe polynomial for
+//          all pairs / a quarter of the pairs
 //          kSweepComp: exponent in float-float (error-free transforms), MUFU exp2, Kahan sums
 //          kSweepF64 : exponent, exp2 and sums in FP64
 //   SIDE   0 = row sweep (Algorithm 1 row update), 1 = column sweep (column update)
@@ -126,19 +154,20 @@ struct Acc<R, kSweepF64> {
 // (<= 170) when R x D <= 12; the rarely run epilogue may spill rather than the hot loop lose warps.
 template <int D, int R, int MODE>
 constexpr int sweep_min_blocks() {
-  return MODE != kSweepFast ? 1 : (R * D <= 4 ? 5 : (R * D <= 12 ? 3 : 1));
+  return !is_fast_mode(MODE) ? 1 : (R * D <= 4 ? 5 : (R * D <= 12 ? 3 : 1));
 }
 
 template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
 __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) sweep_kernel(const Inst* __restrict__ insts,
                                                          const Item* __restrict__ items, int nitems) {
-  static_assert(!(CERT && MODE == kSweepFast), "certificate sweeps use the compensated or FP64 mode");
+  static_assert(!(CERT && is_fast_mode(MODE)), "certificate sweeps use the compensated or FP64 mode");
+  constexpr bool FAST = is_fast_mode(MODE);
   static_assert(UPDATE || (CERT && SIDE == 1), "a non-updating sweep is the standalone certificate");
   constexpr bool ACCN = CERT && SIDE == 1;  // accumulate N_q (Algorithm 2) on the column sweep
   typedef typename PartT<MODE>::type Part;
   constexpr uint32_t kPackTileBytes = kNComp * kTQ * 4;  // one pack tile, all components
   constexpr int kStageFloats = kStageTiles * kNComp * kTQ;
-  constexpr int CH = (MODE == kSweepFast) ? CHF : 8;  // columns per chunk (one max + rescale test)
+  constexpr int CH = FAST ? CHF : 8;  // columns per chunk (one max + rescale test)
   static_assert(CH % 4 == 0 && kTQ % CH == 0, "chunk must divide the tile");
 
   extern __shared__ __align__(128) float smem[];
@@ -237,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         } else {
           st.n[r] = 0.0;
         }
-        if constexpr (MODE == kSweepFast) {
+        if constexpr (FAST) {
           st.acc[r] = 0ull;
           st.M2[r] = 0ull;
         }
@@ -261,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       }
     };
     u64 A2[R][D];
-    if constexpr (MODE == kSweepFast) {
+    if constexpr (FAST) {
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -276,12 +305,12 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       const uint32_t g = gcons + us;
       const int stg = g % kStages;
       const uint32_t par = (g / kStages) & 1u;
-      const bool ok = mbar_wait_bounded(&bars[stg], par, kWaitLimit);
+      const bool ok = mbar_wait_bounded(&bars[stg], par, I->wait_limit);
       const int stage_tiles = min(kStageTiles, ntl - us * kStageTiles);
       for (int tt = 0; tt < stage_tiles; ++tt) {
       const float* __restrict__ S = smem + stg * kStageFloats + tt * (kNComp * kTQ);
 
-      if constexpr (MODE == kSweepFast) {
+      if constexpr (FAST) {
         // Per chunk of CH columns: exponents (f32x2 FMAs), chunk maximum and lazy rescale, then
         // exp2 on the SFU with a pairwise sum.
         u64 va[R][CH / 2];
@@ -359,9 +388,14 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
             u64 e[CH / 2];
 #pragma unroll
             for (int j = 0; j < CH / 2; ++j) {
-              float lo, hi;
-              up2(v[r][j], lo, hi);
-              e[j] = pk2(ex2_mufu(lo), ex2_mufu(hi));
+              // exp2 on the SFU, or by the FMA-pipe polynomial (all pairs, or the first quarter)
+              if (MODE == kSweepFastPoly || (MODE == kSweepFastSplit && j < CH / 8)) {
+                e[j] = exp2_poly2(v[r][j]);
+              } else {
+                float lo, hi;
+                up2(v[r][j], lo, hi);
+                e[j] = pk2(ex2_mufu(lo), ex2_mufu(hi));
+              }
             }
 #pragma unroll
             for (int w = 1; w < CH / 2; w *= 2)
@@ -538,8 +572,9 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       if (!all_ok) {
         if (tid == 0) {
           atomicOr(I->err, kErrTimeout);
-          // let the copies already in flight land before the CTA's shared memory is released
-          for (uint32_t gj = g + 1; gj < gprod; ++gj)
+          // let every copy still in flight (the stage that timed out included) land before the
+          // CTA's shared memory is released; waits on a completed phase return at once
+          for (uint32_t gj = g; gj < gprod; ++gj)
             mbar_wait_bounded(&bars[gj % kStages], (gj / kStages) & 1u, kWaitLimit);
         }
         return;
@@ -631,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         N = (double)Nf - (double)Nc;
       }
       double lse2;
-      if constexpr (MODE == kSweepFast) {
+      if constexpr (FAST) {
         lse2 = mx + (double)__log2f((float)S);  // FP32 log2 is below the FP32 sweep's own rounding
       } else {
         lse2 = mx + log2(S);
@@ -770,13 +805,13 @@ static SweepFn sweep_variant(int v) {
     case 0: return sweep_ptr<D, R, MODE, 0, false, true, CHF>();
     case 1: return sweep_ptr<D, R, MODE, 1, false, true, CHF>();
     case 2:
-      if constexpr (MODE != kSweepFast) return sweep_ptr<D, R, MODE, 1, true, true, CHF>();
+      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, 1, true, true, CHF>();
       return nullptr;
     case 3:
-      if constexpr (MODE != kSweepFast) return sweep_ptr<D, R, MODE, 1, true, false, CHF>();
+      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, 1, true, false, CHF>();
       return nullptr;
     case 4:
-      if constexpr (MODE != kSweepFast) return sweep_ptr<D, R, MODE, 0, true, true, CHF>();
+      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, 0, true, true, CHF>();
       return nullptr;
   }
   return nullptr;
@@ -791,6 +826,16 @@ static SweepFn sweep_m(int mode, int R, int ch, int v) {
     if (R == 2) return ch == 8 ? sweep_variant<D, 2, kSweepFast, 8>(v) : sweep_variant<D, 2, kSweepFast, 16>(v);
     if (R == 4) return ch == 8 ? sweep_variant<D, 4, kSweepFast, 8>(v) : sweep_variant<D, 4, kSweepFast, 16>(v);
     if (R == 8 && ch == 8) return sweep_variant<D, 8, kSweepFast, 8>(v);
+    return nullptr;
+  }
+  if (mode == kSweepFastPoly || mode == kSweepFastSplit) {
+    // the polynomial arms exist for the canonical fast plans only
+    if (R == 2 && ch == 16)
+      return mode == kSweepFastPoly ? sweep_variant<D, 2, kSweepFastPoly, 16>(v)
+                                    : sweep_variant<D, 2, kSweepFastSplit, 16>(v);
+    if (R == 4 && ch == 16)
+      return mode == kSweepFastPoly ? sweep_variant<D, 4, kSweepFastPoly, 16>(v)
+                                    : sweep_variant<D, 4, kSweepFastSplit, 16>(v);
     return nullptr;
   }
   if (mode == kSweepComp) {

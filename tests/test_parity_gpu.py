@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 P = pytest.importorskip("paper_2609_33814_b300")
 
-TOL_POT = {"mufu": 1e-5, "comp": 1e-5, "fp64": 1e-9}
+TOL_POT = {"mufu": 1e-5, "poly": 1e-5, "split": 1e-5, "comp": 1e-5, "fp64": 1e-9}
 TOL_CERT = 1e-6
 
 
@@ -78,7 +78,7 @@ CASES = [("grid16", 1.0, 0), ("grid16", 1.0, 7), ("grid32", 1.0, 3), ("grid16_ga
          ("one_col", 1.0, 2)]
 
 
-@pytest.mark.parametrize("precision", ["mufu", "comp", "fp64"])
+@pytest.mark.parametrize("precision", ["mufu", "poly", "split", "comp", "fp64"])
 @pytest.mark.parametrize("kind,lam,k0", CASES)
 def test_one_step_parity(ctx, kind, lam, k0, precision):
     """The same FP64 state goes into the GPU and the oracle; one iteration of Algorithm 1."""
