@@ -30,29 +30,64 @@ __global__ void pack_coords_kernel(const float* __restrict__ pts, int npts, int 
   if (p < npts) n2[p] = kappa * s;
 }
 
-// Deterministic single-CTA normalisation of weights: w / sum(w), optional floor for zero masses,
-// log w.  Sets err bit kErrNonFinite on a non-positive or non-finite weight.
-__global__ void normalise_weights_kernel(const double* __restrict__ w, int npts, double floor_mass,
-                                         double* __restrict__ wn, double* __restrict__ logw, int* err) {
+// Weight normalisation w / sum(w) with an optional floor for zero masses, and log w, in two
+// launches.  The sum is deterministic: block b adds the fixed range [b * kNormChunk, (b + 1) *
+// kNormChunk) in a fixed order and stores its partial in logw[b] (overwritten by the second
+// launch); the last block to finish adds the partials in block order and stores the total in
+// scratch[0].  scratch[1] is the arrival counter (reset by that block).  Sets err bit
+// kErrNonFinite on a non-positive or non-finite weight.
+constexpr int kNormPer = 16;                    // elements per thread in the sum pass
+constexpr int kNormChunk = kThreads * kNormPer;  // elements per block in the sum pass
+
+__device__ __forceinline__ double floored(double v, double floor_mass) {
+  return (floor_mass > 0.0 && v < floor_mass && v >= 0.0) ? floor_mass : v;
+}
+
+__global__ void weight_sum_kernel(const double* __restrict__ w, int npts, double floor_mass,
+                                  double* __restrict__ logw, double* scratch, int* err) {
   __shared__ double red[kThreads];
+  __shared__ bool last;
   const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * kNormChunk;
   double s = 0.0;
   bool bad = false;
-  for (int i = tid; i < npts; i += kThreads) {
-    double v = w[i];
-    if (floor_mass > 0.0 && v < floor_mass && v >= 0.0) v = floor_mass;
-    bad |= !(v > 0.0) || !isfinite(v);
-    s += v;
-  }
-  const double tot = block_sum(s, red);
-  for (int i = tid; i < npts; i += kThreads) {
-    double v = w[i];
-    if (floor_mass > 0.0 && v < floor_mass && v >= 0.0) v = floor_mass;
-    const double q = v / tot;
-    wn[i] = q;
-    logw[i] = log(q);
+#pragma unroll 4
+  for (int k = 0; k < kNormPer; ++k) {
+    const int i = i0 + k * kThreads + tid;
+    if (i < npts) {
+      const double v = floored(w[i], floor_mass);
+      bad |= !(v > 0.0) || !isfinite(v);
+      s += v;
+    }
   }
   if (bad) atomicOr(err, kErrNonFinite);
+  const double part = block_sum(s, red);
+  if (tid == 0) {
+    logw[blockIdx.x] = part;
+    __threadfence();
+    unsigned* cnt = (unsigned*)(scratch + 1);
+    last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += kThreads) t += __ldcg(logw + b);
+  const double tot = block_sum(t, red);
+  if (tid == 0) {
+    scratch[0] = tot;
+    *(unsigned*)(scratch + 1) = 0u;
+  }
+}
+
+__global__ void weight_log_kernel(const double* __restrict__ w, int npts, double floor_mass,
+                                  const double* __restrict__ scratch, double* __restrict__ wn,
+                                  double* __restrict__ logw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts) return;
+  const double q = floored(w[i], floor_mass) / scratch[0];
+  wn[i] = q;
+  logw[i] = log(q);
 }
 
 // Column pack for iteration k from log beta^{k-1}, log beta^{k-2}:
@@ -135,9 +170,11 @@ cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw, int* err,
-                             cudaStream_t s) {
-  normalise_weights_kernel<<<1, kThreads, 0, s>>>(w, npts, floor_mass, wn, logw, err);
+cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw,
+                             double* scratch, int* err, cudaStream_t s) {
+  weight_sum_kernel<<<(npts + kNormChunk - 1) / kNormChunk, kThreads, 0, s>>>(w, npts, floor_mass, logw, scratch,
+                                                                             err);
+  weight_log_kernel<<<(npts + 255) / 256, 256, 0, s>>>(w, npts, floor_mass, scratch, wn, logw);
   return cudaGetLastError();
 }
 

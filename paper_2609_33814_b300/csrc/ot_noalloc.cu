@@ -107,6 +107,8 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
   h.nms[0][0] = splits;  // fast row sweep: one micro-split per split
   h.ms_tiles[0][0] = tps;
   h.wait_limit = kWaitLimit;
+  h.hint[0] = h.hint[1] = nullptr;  // a single sweep at k = 0: no shift hints
+  h.hint_bad = nullptr;
   h.kappa = kappa;
   h.eta = eps;       // k = 0 and lambda = 1 give the sweep temperature eta / (lambda k + 1) = eps
   h.lambda = 1.0;

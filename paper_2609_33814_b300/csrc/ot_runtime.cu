@@ -22,8 +22,8 @@ cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int n
                          cudaStream_t stream);
 cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
                                double* n2, cudaStream_t s);
-cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw, int* err,
-                             cudaStream_t s);
+cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw,
+                             double* scratch, int* err, cudaStream_t s);
 cudaError_t launch_repack_cols(const Inst* I, int m, cudaStream_t s);
 cudaError_t launch_pair_cost_range(const float* x, int n, const float* y, int m, int d, unsigned* mx,
                                    unsigned* mn, int sms, cudaStream_t s);
@@ -281,6 +281,7 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   L.yn2 = cv.take<double>(m);
   L.state0 = cv.take<double>(2 * n + 5 * m);  // alpha, alpha_hat, beta, beta_prev, beta_hat, tilde, tilde_next
   L.fg = cv.take<double>(2 * (n + m));         // f_cur, g_cur, f_best, g_best
+  L.hint = cv.take<float>(n + m);              // shift hints, row side then column side
   L.part = cv.take<PartF64>(nsp);
   L.cnt = cv.take<unsigned>(maxblk + 1);
   L.maxblk = maxblk;
@@ -336,6 +337,8 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
   double* fg = (double*)(base + o_fg);
   h.f_cur = fg;
   h.g_cur = fg + n;
+  h.hint[0] = (float*)(base + L.hint);
+  h.hint[1] = h.hint[0] + n;
   in.f_best = fg + n + m;
   in.g_best = fg + 2 * n + m;
   h.part = base + o_part;
@@ -346,6 +349,7 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
   h.cert = ctrl;
   h.k = (long long*)(ctrl + 8);
   h.err = (int*)(ctrl + 9);
+  h.hint_bad = (int*)(ctrl + 14);  // ctrl[14..15]: four hint-miss counters (zeroed: see the k >= 1 rule)
   in.ctrl = ctrl;
   unsigned* range = (unsigned*)(base + o_range);
   in.d_inst = (Inst*)(base + o_inst);
@@ -393,9 +397,10 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
 
   OT_CUDA(launch_pack_coords(in.xraw, (int)n, in.d, h.tiles_x, kappa, h.xpack, (double*)h.xn2, s));
   OT_CUDA(launch_pack_coords(in.yraw, (int)m, in.d, h.tiles_y, kappa, h.ypack, (double*)h.yn2, s));
-  OT_CUDA(launch_normalise(ain, (int)n, p->zero_mass_floor, (double*)h.a, (double*)h.log_a, h.err, s));
-  OT_CUDA(launch_normalise(bin, (int)m, p->zero_mass_floor, (double*)h.b, (double*)h.log_b, h.err, s));
-  ctx.launches += 4;
+  // ctrl[10..13]: scratch of the two normalisations (total, arrival counter), zeroed above
+  OT_CUDA(launch_normalise(ain, (int)n, p->zero_mass_floor, (double*)h.a, (double*)h.log_a, ctrl + 10, h.err, s));
+  OT_CUDA(launch_normalise(bin, (int)m, p->zero_mass_floor, (double*)h.b, (double*)h.log_b, ctrl + 12, h.err, s));
+  ctx.launches += 6;
 
   std::vector<Item> items;
   for (const LaunchPlan* pl : {&in.fast, &in.cert}) {
@@ -814,6 +819,10 @@ ot_status ot_state_set(ot_state* st, int which, const double* in_vec, int64_t k)
   OT_CUDA(cudaMemcpyAsync(p, in_vec, len * sizeof(double), cudaMemcpyHostToDevice, in.stream));
   const long long kk = k;
   OT_CUDA(cudaMemcpyAsync(in.h.k, &kk, sizeof(kk), cudaMemcpyHostToDevice, in.stream));
+  // the stored shift hints belong to the replaced state: mark both sides as missed, so the next
+  // iteration runs without them and re-validates its own
+  static const int kMissed[4] = {1, 1, 1, 1};
+  OT_CUDA(cudaMemcpyAsync(in.h.hint_bad, kMissed, sizeof(kMissed), cudaMemcpyHostToDevice, in.stream));
   OT_CUDA(launch_repack_cols(in.d_inst, (int)in.m, in.stream));
   ctx.launches += 1;
   OT_CUDA(cudaStreamSynchronize(in.stream));

@@ -53,8 +53,8 @@ struct LaunchPlan {
 
 // Byte offsets of an instance's buffers inside its single device allocation.
 struct Layout {
-  size_t xpack, ypack, xraw, yraw, a, b, ain, bin, la, lb, xn2, yn2, state0, fg, part, cnt, blk, ctrl, range, inst,
-      items;
+  size_t xpack, ypack, xraw, yraw, a, b, ain, bin, la, lb, xn2, yn2, state0, fg, hint, part, cnt, blk, ctrl, range,
+      inst, items;
   size_t maxblk;
 };
 

@@ -33,6 +33,14 @@ namespace ot {
 constexpr double kLog2e = 1.4426950408889634074;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr float kTau = 32.0f;            // lazy-rescale threshold (base-2 units above the shift)
+// A validated hint E (see Inst::hint) starts a micro-split's running shift at floor(E) - kHintMargin
+// (never below its first chunk's maximum), so the terms near the row's maximum stay below 2^(8 +
+// the hint's error) and a tile sum only overflows 2^64 if the hint is ~48 too low.  Terms more
+// than 126 below the shift flush to zero: at most m 2^(E - L - 134) of the total 2^L, which the
+// epilogue keeps below 2^-38 by rejecting a sweep whose hint exceeded L by more than kHintGuard.
+constexpr float kHintMargin = 8.0f;
+constexpr float kHintTol = 16.0f;
+constexpr float kHintGuard = 72.0f;
 constexpr float kPadH = -1.0e30f;        // h of padding points: contributes exp2(-1e30) = 0
 
 // ---------------------------------------------------------------------------------------------
@@ -297,6 +305,18 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         for (int k = 0; k < D; ++k) A2[r][k] = pk2(Ah[r][k], Ah[r][k]);
     }
 
+    // running-shift floor of each point from its validated hint (fast sweeps, k >= 1)
+    float hs[R];
+    bool use_hint = false;
+    if constexpr (FAST) {
+      use_hint = kiter >= 1 && I->hint_bad != nullptr && __ldcg(&I->hint_bad[2 * SIDE + ((kiter - 1) & 1)]) == 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+        hs[r] = (use_hint && p < np) ? floorf(__ldcg(&I->hint[SIDE][p])) - kHintMargin : -INFINITY;
+      }
+    }
+
     const int nst = (ntl + kStageTiles - 1) / kStageTiles;  // pipeline stages of this item
 
     bool fresh = true;
@@ -364,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
 #pragma unroll
             for (int r = 0; r < R; ++r) {
               if (fresh || cm[r] > kTau) {
-                const float sh = floorf(cm[r]);
+                const float sh = fresh ? fmaxf(floorf(cm[r]), hs[r]) : floorf(cm[r]);
                 if (!fresh) {
                   const float f = exp2_neg_int(sh);
                   st.acc[r] = mul2(st.acc[r], pk2(f, f));
@@ -597,6 +617,8 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     const double inv_eps1 = 1.0 / eps_of(I, kiter + 1);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     bool bad = false;
+    bool hmiss = false;  // a stored hint missed this sweep's log-sum-exp by more than kHintTol
+    float* const hint = UPDATE ? I->hint[SIDE] : nullptr;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
@@ -671,6 +693,13 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       } else {
         lse2 = mx + log2(S);
       }
+      if (hint != nullptr) {
+        const float e = __ldcg(&hint[p]);
+        const float l = (float)lse2;
+        hmiss |= kiter == 0 || !(fabsf(e - l) <= kHintTol);
+        bad |= use_hint && e - l > kHintGuard;  // flushed terms could matter: reject the sweep
+        hint[p] = (float)(lse2 * eps * inv_eps1);
+      }
       if constexpr (SIDE == 0) {
         const double lse = lse2 * kLn2 - I->xn2[p] * inv_eps;
         const double lah = I->log_a[p] - lse;
@@ -716,6 +745,8 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       }
     }
     if (bad) atomicOr(I->err, kErrNonFinite);
+    if (hint != nullptr && __syncthreads_or(hmiss ? 1 : 0) && tid == 0)
+      atomicAdd(&I->hint_bad[2 * SIDE + (kiter & 1)], 1);
     if constexpr (CERT) {
       const double s0 = block_sum(acc0, red);
       if constexpr (SIDE == 0) {
@@ -781,7 +812,14 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         }
       }
       if (tid == 0) {
-        if constexpr (UPDATE) *I->k = kiter + 1;
+        if constexpr (UPDATE) {
+          *I->k = kiter + 1;
+          // the counters iteration kiter + 1 fills (last read by iteration kiter)
+          if (I->hint_bad != nullptr) {
+            I->hint_bad[(kiter + 1) & 1] = 0;
+            I->hint_bad[2 + ((kiter + 1) & 1)] = 0;
+          }
+        }
         *I->done = 0u;
       }
     }

@@ -165,6 +165,34 @@ def test_fp32_trajectory_error_is_small(ctx, precision):
     assert abs(res["L_best"] - ro["L_best"]) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", ["mufu", "split"])
+@pytest.mark.parametrize("kind,lam,k", [("grid32", 1.0, 1200), ("grid16_gauss", 1.5, 600), ("ragged3", 1.0, 300)])
+def test_hinted_sweep_late_iteration(ctx, precision, kind, lam, k):
+    """Late iterations (small eps, wide exponent ranges) where the fast sweeps start their running
+    shifts from the previous iteration's log-sum-exp: the GPU's iteration k + 1 against the oracle's
+    iteration from the GPU's own state after k iterations."""
+    prob = _problem(kind, 21)
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0, lam=lam,
+                  precision=precision, cert_every=0)
+    S.step(k)
+    eps_prev = O.eps_schedule(1.0, lam, k - 1)
+    st = O.DualState(S.get(P.OT_LOG_ALPHA), S.get(P.OT_LOG_BETA), S.get(P.OT_LOG_BETA_PREV),
+                     S.get(P.OT_LOG_ALPHA_HAT), S.get(P.OT_LOG_BETA_HAT), S.get(P.OT_LOG_BETA_TILDE), k, eps_prev)
+    a = prob.a / prob.a.sum()
+    b = prob.b / prob.b.sum()
+    for _ in range(3):
+        st = O.dual_obdrs_step(st, np.log(a), np.log(b), C, 1.0, lam)
+        S.step(1)
+        err = _potential_err(st, S.get(P.OT_LOG_ALPHA_HAT), S.get(P.OT_LOG_BETA_HAT), st.eps, np.log(b))
+        assert err <= TOL_POT[precision], (st.k, err)
+        # continue the oracle from the GPU's state: each comparison covers one iteration
+        st = O.DualState(S.get(P.OT_LOG_ALPHA), S.get(P.OT_LOG_BETA), S.get(P.OT_LOG_BETA_PREV),
+                         S.get(P.OT_LOG_ALPHA_HAT), S.get(P.OT_LOG_BETA_HAT), S.get(P.OT_LOG_BETA_TILDE), st.k,
+                         st.eps)
+    S.close()
+
+
 def test_cost_scale_from_device_max(ctx):
     """cost_scale = 0: kappa = 1 / max pair cost (App. G) computed on the device."""
     prob = I.rgb_problem(3000, seed=8, m=2500)
