@@ -34,7 +34,7 @@ constexpr size_t kOffAlpha = kOffYN2 + align256(kMaxPts * sizeof(double));
 constexpr size_t kOffTilde = kOffAlpha + align256(kMaxPts * sizeof(double));
 constexpr size_t kOffPart = kOffTilde + align256(kMaxPts * sizeof(double));
 constexpr size_t kOffCnt = kOffPart + align256((size_t)kMaxSplits * kMaxPts * sizeof(float4));
-constexpr size_t kOffCtrl = kOffCnt + align256((kMaxBlocks + 2) * sizeof(unsigned));
+constexpr size_t kOffCtrl = kOffCnt + align256((kMaxBlocks + 4) * sizeof(unsigned));
 constexpr size_t kOffInst = kOffCtrl + align256(16 * sizeof(double));
 constexpr size_t kOffItems = kOffInst + align256(sizeof(Inst));
 constexpr size_t kScratchBytes = kOffItems + align256((size_t)kMaxBlocks * kMaxSplits * sizeof(Item));
@@ -135,7 +135,7 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
   Item* d_items = (Item*)(base + kOffItems);
 
   // every call shares the scratch: clear the counters, k, the error bits and the relaxation input
-  if (cudaMemsetAsync(h.cnt, 0, (kMaxBlocks + 2) * sizeof(unsigned), s) != cudaSuccess ||
+  if (cudaMemsetAsync(h.cnt, 0, (kMaxBlocks + 4) * sizeof(unsigned), s) != cudaSuccess ||
       cudaMemsetAsync(ctrl, 0, 16 * sizeof(double), s) != cudaSuccess ||
       cudaMemsetAsync(h.log_alpha, 0, n * sizeof(double), s) != cudaSuccess)
     return OT_ECUDA;
@@ -147,7 +147,8 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
       launch_repack_cols(d_inst, (int)m, s) != cudaSuccess)
     return OT_ECUDA;
   const int grid = nitems < resident ? nitems : resident;
-  if (launch_sweep(fn, d_inst, d_items, nitems, grid, s) != cudaSuccess) return OT_ECUDA;
+  unsigned* sched = h.cnt + kMaxBlocks + 2;  // work-item ticket counters
+  if (launch_sweep(fn, d_inst, d_items, nitems, grid, sched, s) != cudaSuccess) return OT_ECUDA;
   int err = 0;
   if (cudaMemcpyAsync(&err, h.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

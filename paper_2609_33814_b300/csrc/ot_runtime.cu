@@ -19,7 +19,7 @@ namespace ot {
 
 size_t sweep_smem_bytes();
 cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
-                         cudaStream_t stream);
+                         unsigned* sched, cudaStream_t stream);
 cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
                                double* n2, cudaStream_t s);
 cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw,
@@ -283,7 +283,7 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   L.fg = cv.take<double>(2 * (n + m));         // f_cur, g_cur, f_best, g_best
   L.hint = cv.take<float>(n + m);              // shift hints, row side then column side
   L.part = cv.take<PartF64>(nsp);
-  L.cnt = cv.take<unsigned>(maxblk + 1);
+  L.cnt = cv.take<unsigned>(maxblk + 3);  // point-block counters, epilogue counter, 2 scheduler counters
   L.maxblk = maxblk;
   L.blk = cv.take<double>((n + kThreads - 1) / kThreads + 3 * ((m + kThreads - 1) / kThreads));
   L.ctrl = cv.take<double>(16);
@@ -344,6 +344,7 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
   h.part = base + o_part;
   h.cnt = (unsigned*)(base + o_cnt);
   h.done = h.cnt + maxblk;
+  in.sched = h.cnt + maxblk + 1;
   h.blk = (double*)(base + o_blk);
   double* ctrl = (double*)(base + o_ctrl);
   h.cert = ctrl;
@@ -462,10 +463,10 @@ static cudaError_t issue_iteration(Instance& in, bool cert, cudaEvent_t* ev = nu
   SweepFn fc = get_sweep(in.d, pl.mode, pl.R, pl.ch, cert ? 2 : 1);
   cudaError_t e;
   if (ev && (e = cudaEventRecordWithFlags(ev[0], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-  e = launch_sweep(fr, in.d_inst, pl.d_row, pl.n_row, pl.grid_row, in.stream);
+  e = launch_sweep(fr, in.d_inst, pl.d_row, pl.n_row, pl.grid_row, in.sched, in.stream);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecordWithFlags(ev[1], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-  e = launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.stream);
+  e = launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.sched, in.stream);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecordWithFlags(ev[2], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -633,7 +634,7 @@ ot_status run_iterations(Context& ctx, Instance& in, int64_t n_iters, bool stop_
 ot_status standalone_certificate(Context& ctx, Instance& in) {
   const LaunchPlan& pl = in.cert;
   SweepFn fc = get_sweep(in.d, pl.mode, pl.R, pl.ch, 3);
-  OT_CUDA(launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.stream));
+  OT_CUDA(launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.sched, in.stream));
   ctx.launches += 1;
   return read_ctrl(ctx, in);
 }

@@ -11,7 +11,7 @@
 
 namespace ot {
 
-typedef void (*SweepFn)(const Inst*, const Item*, int);
+typedef void (*SweepFn)(const Inst*, const Item*, int, unsigned*);
 SweepFn get_sweep(int d, int mode, int R, int ch, int variant);
 
 // Accumulated timing of one kind of sweep launch (profiling mode).
@@ -70,6 +70,7 @@ struct Instance {
   double* f_best = nullptr;
   double* g_best = nullptr;
   double* ctrl = nullptr;        // device control block: cert record, k, error bits
+  unsigned* sched = nullptr;     // work-item ticket counters of this instance's sweeps (inside mem)
   double* h_ctrl = nullptr;      // pinned host copy
   cudaStream_t stream = nullptr;
   ot_params params{};
@@ -107,7 +108,7 @@ ot_status read_ctrl(Context& ctx, Instance& in);
 ot_status absorb_cert(Context& ctx, Instance& in);
 void fill_result(const Instance& in, ot_result* r);
 cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
-                         cudaStream_t stream);
+                         unsigned* sched, cudaStream_t stream);
 void instance_free(Instance& in);
 ot_status run_iterations(Context& ctx, Instance& in, int64_t n_iters, bool stop_rule, bool final_cert);
 ot_status standalone_certificate(Context& ctx, Instance& in);

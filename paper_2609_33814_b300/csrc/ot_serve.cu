@@ -64,6 +64,7 @@ struct Lane {
   Item* h_items = nullptr;
   size_t items_cap = 0;
   int off[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, grid[4] = {0, 0, 0, 0};
+  unsigned* d_sched = nullptr;         // work-item ticket counters of the lane's launches
   double entries_per_sweep = 0;        // sum of n * m over the active instances
   std::vector<cudaEvent_t> evs;        // profiling: one event between consecutive launches
   bool timed = false;                  // the last chunk recorded events
@@ -181,6 +182,10 @@ void Server::run_chunk(Lane& L) {
   const size_t na = L.active.size();
   if (L.dirty) {
     // instance table and work items of the four launch kinds for the current composition
+    if (!L.d_sched) {
+      cudaMalloc(&L.d_sched, 2 * sizeof(unsigned));
+      cudaMemsetAsync(L.d_sched, 0, 2 * sizeof(unsigned), s);
+    }
     if (L.table_cap < na) {
       if (L.d_table) cudaFree(L.d_table);
       if (L.h_table) cudaFreeHost(L.h_table);
@@ -258,7 +263,7 @@ void Server::run_chunk(Lane& L) {
     const bool cert = it == L.ce - 1;
     for (int side = 0; side < 2; ++side) {
       const int kind = (cert ? 2 : 0) + side;
-      launch_sweep(fns[kind], L.d_table, L.d_items + L.off[kind], L.cnt[kind], L.grid[kind], s);
+      launch_sweep(fns[kind], L.d_table, L.d_items + L.off[kind], L.cnt[kind], L.grid[kind], L.d_sched, s);
       ctx.launches += 1;
       if (profile) cudaEventRecord(L.evs[2 * it + side + 1], s);
     }
@@ -490,6 +495,7 @@ void ot_serve_destroy(ot_server* sv) {
     }
     if (L.d_table) cudaFree(L.d_table);
     if (L.h_table) cudaFreeHost(L.h_table);
+    if (L.d_sched) cudaFree(L.d_sched);
     if (L.d_items) cudaFree(L.d_items);
     if (L.h_items) cudaFreeHost(L.h_items);
     for (cudaEvent_t e : L.evs) cudaEventDestroy(e);

@@ -165,9 +165,13 @@ constexpr int sweep_min_blocks() {
   return !is_fast_mode(MODE) ? 1 : (R * D <= 4 ? 5 : (R * D <= 12 ? 3 : 1));
 }
 
+// Work distribution: items are handed out in index order (the host sorts them longest first) from
+// the ticket counter sched[0]; sched[1] counts CTAs that have finished, and the last one resets
+// both, so consecutive launches on a stream can share the two counters.
 template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
 __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) sweep_kernel(const Inst* __restrict__ insts,
-                                                         const Item* __restrict__ items, int nitems) {
+                                                         const Item* __restrict__ items, int nitems,
+                                                         unsigned* __restrict__ sched) {
   static_assert(!(CERT && is_fast_mode(MODE)), "certificate sweeps use the compensated or FP64 mode");
   constexpr bool FAST = is_fast_mode(MODE);
   static_assert(UPDATE || (CERT && SIDE == 1), "a non-updating sweep is the standalone certificate");
@@ -182,6 +186,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ double red[kThreads];
   __shared__ int s_flag;
+  __shared__ int s_ring[8];  // item indices in the order the producer took them (<= kStages + 1 ahead)
 
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -191,13 +196,18 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   }
   __syncthreads();
 
-  // The TMA pipeline runs across work items: thread 0 keeps kStages stages in flight, moving on to
-  // the CTA's next item (it + gridDim.x) before the current one ends, so it never drains.
+  // The TMA pipeline runs across work items: thread 0 keeps kStages stages in flight, taking the
+  // CTA's next item from the ticket counter before the current one ends, so it never drains.  The
+  // item index reaches the other threads through s_ring: it is written before the stage that
+  // needs it is issued, hence before a CTA barrier that every consumer of that item passes.
   uint32_t gcons = 0;  // stages consumed by this CTA (stage slot and mbarrier parity)
   uint32_t gprod = 0;  // stages issued by this CTA
-  int pr_it = blockIdx.x, pr_us = 0, pr_nst = 0, pr_qt0 = 0, pr_ntl = 0;
+  uint32_t pseq = 0;   // items taken by this CTA
+  int pr_it = 0, pr_us = 0, pr_nst = 0, pr_qt0 = 0, pr_ntl = 0;
   const float* pr_qpack = nullptr;
   auto pr_load = [&]() {
+    pr_it = (int)atomicAdd(&sched[0], 1u);
+    s_ring[pseq++ & 7u] = pr_it;
     if (pr_it >= nitems) return;
     const Item itp = items[pr_it];
     const Inst* Ip = insts + itp.inst;
@@ -217,17 +227,18 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     bulk_g2s(smem + stg * kStageFloats, pr_qpack + (size_t)(pr_qt0 + pr_us * kStageTiles) * kNComp * kTQ,
              tiles * kPackTileBytes, &bars[stg]);
     ++gprod;
-    if (++pr_us == pr_nst) {
-      pr_it += gridDim.x;
-      pr_load();
-    }
+    if (++pr_us == pr_nst) pr_load();
   };
   if (tid == 0) {
     pr_load();
     for (int j = 0; j < kStages; ++j) produce();
   }
+  __syncthreads();
 
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  bool aborted = false;
+  for (uint32_t cseq = 0;; ++cseq) {
+    const int it = s_ring[cseq & 7u];
+    if (it >= nitems) break;
     const Item item = items[it];
     const Inst* __restrict__ I = insts + item.inst;
     const int np = SIDE == 0 ? I->n : I->m;
@@ -597,10 +608,12 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           for (uint32_t gj = g; gj < gprod; ++gj)
             mbar_wait_bounded(&bars[gj % kStages], (gj / kStages) & 1u, kWaitLimit);
         }
-        return;
+        aborted = true;
+        break;
       }
       if (tid == 0) produce();  // refill the slot just consumed (possibly with the next item's tiles)
     }
+    if (aborted) break;
     gcons += nst;
 
     // ---- last CTA of this point block runs the epilogue ----
@@ -824,12 +837,20 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       }
     }
   }
+  // the last CTA out resets the scheduler (every CTA has taken its final ticket by now)
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
+      sched[0] = 0u;
+      sched[1] = 0u;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
 // Launch table: one entry per instantiated (D, R, MODE, SIDE, CERT, UPDATE).
 // ---------------------------------------------------------------------------------------------
-typedef void (*SweepFn)(const Inst*, const Item*, int);
+typedef void (*SweepFn)(const Inst*, const Item*, int, unsigned*);
 
 template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
 static SweepFn sweep_ptr() {
