@@ -215,9 +215,9 @@ ot_status ot_serve_cancel(ot_server* sv, uint64_t req_id);
 ot_status ot_serve_stats(ot_server* sv, ot_serve_statistics* out);
 /* Zero the statistics, kernel timings and launch count. */
 ot_status ot_serve_reset_stats(ot_server* sv);
-/* Kernel timing of the server's batched sweeps (as ot_profile_enable / ot_profile_read: kinds
- * 0 fast row, 1 fast column, 2 certificate row, 3 certificate column; entries = sum of n * m over
- * the instances a launch covers). */
+/* Kernel timing of the server's batched launches (as ot_profile_enable / ot_profile_read: kind 0
+ * the fast iterations of a chunk, kind 1 its certificate iteration; entries = 2 n m per iteration,
+ * summed over the instances a launch covers). */
 ot_status ot_serve_profile_enable(ot_server* sv, int on);
 ot_status ot_serve_profile_read(ot_server* sv, int kind, int64_t* launches, double* entries, double* ms);
 void ot_serve_destroy(ot_server* sv);
@@ -246,11 +246,12 @@ ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, const float* x,
                                 double* log_alpha_hat, uint64_t stream);
 
 /* Measurement support (not part of the method): kernel timing.  While enabled on a context, every
- * iteration chunk of its states records a CUDA event on the launching stream before and after each
- * sweep launch (inside the captured CUDA graph) and waits for the chunk, and per kind of sweep
- * (0 fast row, 1 fast column, 2 certificate row, 3 certificate column) the number of launches,
- * the algorithmic implicit entries (n * m per sweep) and the summed event durations (ms) accumulate.
- * Any output pointer may be NULL. */
+ * iteration chunk of its states records CUDA events on the launching stream around its launches
+ * (inside the captured CUDA graph) and waits for the chunk.  A chunk is one launch for its fast
+ * iterations (row and column sweeps of every iteration) and one for its certificate iteration; per
+ * kind (0 fast iterations, 1 certificate iterations) the number of launches, the algorithmic
+ * implicit entries (2 n m per iteration) and the summed event durations (ms) accumulate.  Other
+ * kinds return OT_EINVAL.  Any output pointer may be NULL. */
 ot_status ot_profile_enable(ot_context* ctx, int on);
 ot_status ot_profile_reset(ot_context* ctx);
 ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* entries, double* ms);

@@ -343,7 +343,8 @@ class Server:
         _lib.ot_serve_profile_enable(self._h, 1 if on else 0)
 
     def kernel_stats(self, kind: int):
-        """(launches, entries, ms) of one kind of batched sweep since the last reset."""
+        """(launches, entries, ms) since the last reset of kind 0 (fast iterations) or 1 (certificate
+        iterations); entries count both sweeps of every iteration."""
         n, e, ms = C.c_int64(), C.c_double(), C.c_double()
         _lib.ot_serve_profile_read(self._h, int(kind), C.byref(n), C.byref(e), C.byref(ms))
         return n.value, e.value, ms.value

@@ -107,6 +107,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Acquire load / release store of a 64-bit counter at GPU scope (phase signals between CTAs of
+// one launch; they also bypass the SM's L1, which is not coherent).
+__device__ __forceinline__ long long ld_acquire(const long long* p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(long long* p, long long v) {
+  asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// Orders this thread's view of global memory (generic proxy) before its later bulk copies (async
+// proxy): needed before a TMA copy reads data that another CTA of the same launch wrote.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // Bounded wait: returns false after `limit` polls (the caller records an error and stops).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i)

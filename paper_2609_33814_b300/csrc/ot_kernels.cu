@@ -156,10 +156,10 @@ SweepFn get_sweep(int d, int mode, int R, int ch, int variant) {
 }
 size_t sweep_smem_bytes() { return (size_t)kStages * kStageTiles * kNComp * kTQ * sizeof(float); }
 
-cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
+cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int iters, int grid,
                          unsigned* sched, cudaStream_t stream) {
-  if (nitems <= 0) return cudaSuccess;
-  void* args[] = {(void*)&insts, (void*)&items, (void*)&nitems, (void*)&sched};
+  if (nitems <= 0 || iters <= 0 || grid <= 0) return cudaSuccess;
+  void* args[] = {(void*)&insts, (void*)&items, (void*)&nitems, (void*)&iters, (void*)&sched};
   return cudaLaunchKernel((const void*)fn, dim3(grid), dim3(kThreads), args, sweep_smem_bytes(), stream);
 }
 

@@ -74,7 +74,9 @@ struct Inst {
   // when the previous iteration of the same side had no miss.  Null: no hints.
   float* hint[2];                // row side (n floats), column side (m floats)
   int* hint_bad;                 // 4 counters
-  long long* k;                  // completed iterations
+  long long* k;                  // completed iterations (released by the last column epilogue)
+  long long* rows;               // completed row sweeps (released by the last row epilogue)
+  long long* k0;                 // k at the start of the current launch (set by the previous one)
   double* cert;                  // certificate record (kCertLen doubles)
   int* err;                      // error bits
 };
@@ -84,10 +86,11 @@ struct alignas(32) PartF64 {
   double x, y, z, w;
 };
 
-// A unit of sweep work: instance, point block (kThreads * R points of the launched kernel), and a
-// run of consecutive micro-splits of the reduced side: first one and count.
+// A unit of sweep work: instance, side (0 row sweep, 1 column sweep), point block (kThreads * R
+// points of the launched kernel), and a run of consecutive micro-splits of the reduced side: first
+// one and count.
 struct Item {
-  int inst, pblk, ms0, nms;
+  int inst, side, pblk, ms0, nms;
 };
 
 }  // namespace ot

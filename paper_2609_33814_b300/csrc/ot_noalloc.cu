@@ -34,8 +34,8 @@ constexpr size_t kOffAlpha = kOffYN2 + align256(kMaxPts * sizeof(double));
 constexpr size_t kOffTilde = kOffAlpha + align256(kMaxPts * sizeof(double));
 constexpr size_t kOffPart = kOffTilde + align256(kMaxPts * sizeof(double));
 constexpr size_t kOffCnt = kOffPart + align256((size_t)kMaxSplits * kMaxPts * sizeof(float4));
-constexpr size_t kOffCtrl = kOffCnt + align256((kMaxBlocks + 4) * sizeof(unsigned));
-constexpr size_t kOffInst = kOffCtrl + align256(16 * sizeof(double));
+constexpr size_t kOffCtrl = kOffCnt + align256((kMaxBlocks + 6) * sizeof(unsigned));
+constexpr size_t kOffInst = kOffCtrl + align256(24 * sizeof(double));
 constexpr size_t kOffItems = kOffInst + align256(sizeof(Inst));
 constexpr size_t kScratchBytes = kOffItems + align256((size_t)kMaxBlocks * kMaxSplits * sizeof(Item));
 
@@ -49,7 +49,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 __global__ void noalloc_setup_kernel(Inst inst, Inst* dst, Item* items, int pblks, int splits) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) *dst = inst;
-  if (i < pblks * splits) items[i] = Item{0, i % pblks, i / pblks, 1};
+  if (i < pblks * splits) items[i] = Item{0, 0, i % pblks, i / pblks, 1};
 }
 
 static std::mutex g_mu;
@@ -131,12 +131,14 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
   h.cert = ctrl;
   h.k = (long long*)(ctrl + 8);
   h.err = (int*)(ctrl + 9);
+  h.rows = (long long*)(ctrl + 16);  // k = k0 = 0: the row items wait for nothing
+  h.k0 = (long long*)(ctrl + 17);
   Inst* d_inst = (Inst*)(base + kOffInst);
   Item* d_items = (Item*)(base + kOffItems);
 
   // every call shares the scratch: clear the counters, k, the error bits and the relaxation input
-  if (cudaMemsetAsync(h.cnt, 0, (kMaxBlocks + 4) * sizeof(unsigned), s) != cudaSuccess ||
-      cudaMemsetAsync(ctrl, 0, 16 * sizeof(double), s) != cudaSuccess ||
+  if (cudaMemsetAsync(h.cnt, 0, (kMaxBlocks + 6) * sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(ctrl, 0, 24 * sizeof(double), s) != cudaSuccess ||
       cudaMemsetAsync(h.log_alpha, 0, n * sizeof(double), s) != cudaSuccess)
     return OT_ECUDA;
   const int nitems = pblks * splits;
@@ -147,8 +149,8 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
       launch_repack_cols(d_inst, (int)m, s) != cudaSuccess)
     return OT_ECUDA;
   const int grid = nitems < resident ? nitems : resident;
-  unsigned* sched = h.cnt + kMaxBlocks + 2;  // work-item ticket counters
-  if (launch_sweep(fn, d_inst, d_items, nitems, grid, sched, s) != cudaSuccess) return OT_ECUDA;
+  unsigned* sched = h.cnt + kMaxBlocks + 2;  // scheduler counters (3)
+  if (launch_sweep(fn, d_inst, d_items, nitems, 1, grid, sched, s) != cudaSuccess) return OT_ECUDA;
   int err = 0;
   if (cudaMemcpyAsync(&err, h.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

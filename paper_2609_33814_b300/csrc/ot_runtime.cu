@@ -18,7 +18,7 @@
 namespace ot {
 
 size_t sweep_smem_bytes();
-cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
+cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int iters, int grid,
                          unsigned* sched, cudaStream_t stream);
 cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
                                double* n2, cudaStream_t s);
@@ -143,15 +143,14 @@ void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl) {
   pl.group_col = solo_group(pl.pblk_col, pl.nms_col, resident);
   pl.n_row = pl.pblk_row * ((pl.nms_row + pl.group_row - 1) / pl.group_row);
   pl.n_col = pl.pblk_col * ((pl.nms_col + pl.group_col - 1) / pl.group_col);
-  pl.grid_row = std::min(pl.n_row, resident);
-  pl.grid_col = std::min(pl.n_col, resident);
+  pl.resident = resident;
 }
 
 // Work items of one sweep of one instance: every point block times runs of `group` consecutive
 // micro-splits (the last run may be shorter).
-void build_items(std::vector<Item>& out, int inst, int pblks, int nms, int group) {
+void build_items(std::vector<Item>& out, int inst, int side, int pblks, int nms, int group) {
   for (int m0 = 0; m0 < nms; m0 += group)
-    for (int b = 0; b < pblks; ++b) out.push_back(Item{inst, b, m0, std::min(group, nms - m0)});
+    for (int b = 0; b < pblks; ++b) out.push_back(Item{inst, side, b, m0, std::min(group, nms - m0)});
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -283,10 +282,10 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   L.fg = cv.take<double>(2 * (n + m));         // f_cur, g_cur, f_best, g_best
   L.hint = cv.take<float>(n + m);              // shift hints, row side then column side
   L.part = cv.take<PartF64>(nsp);
-  L.cnt = cv.take<unsigned>(maxblk + 3);  // point-block counters, epilogue counter, 2 scheduler counters
+  L.cnt = cv.take<unsigned>(maxblk + 4);  // point-block counters, epilogue counter, 3 scheduler counters
   L.maxblk = maxblk;
   L.blk = cv.take<double>((n + kThreads - 1) / kThreads + 3 * ((m + kThreads - 1) / kThreads));
-  L.ctrl = cv.take<double>(16);
+  L.ctrl = cv.take<double>(24);
   L.range = cv.take<unsigned>(2);
   L.inst = cv.take<Inst>(1);
   const size_t n_items = (size_t)in.fast.n_row + in.fast.n_col + in.cert.n_row + in.cert.n_col;
@@ -351,6 +350,8 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
   h.k = (long long*)(ctrl + 8);
   h.err = (int*)(ctrl + 9);
   h.hint_bad = (int*)(ctrl + 14);  // ctrl[14..15]: four hint-miss counters (zeroed: see the k >= 1 rule)
+  h.rows = (long long*)(ctrl + 16);
+  h.k0 = (long long*)(ctrl + 17);
   in.ctrl = ctrl;
   unsigned* range = (unsigned*)(base + o_range);
   in.d_inst = (Inst*)(base + o_inst);
@@ -405,8 +406,8 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
 
   std::vector<Item> items;
   for (const LaunchPlan* pl : {&in.fast, &in.cert}) {
-    build_items(items, 0, pl->pblk_row, pl->nms_row, pl->group_row);
-    build_items(items, 0, pl->pblk_col, pl->nms_col, pl->group_col);
+    build_items(items, 0, 0, pl->pblk_row, pl->nms_row, pl->group_row);
+    build_items(items, 0, 1, pl->pblk_col, pl->nms_col, pl->group_col);
   }
   OT_CUDA(cudaMemcpyAsync(items_base, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, s));
   OT_CUDA(cudaMemcpyAsync(in.d_inst, &h, sizeof(Inst), cudaMemcpyHostToDevice, s));
@@ -457,24 +458,40 @@ void instance_free(Instance& in) {
 // ---------------------------------------------------------------------------------------------
 // Iterations
 // ---------------------------------------------------------------------------------------------
-static cudaError_t issue_iteration(Instance& in, bool cert, cudaEvent_t* ev = nullptr) {
+// `iters` iterations of one plan as one launch (row and column sweeps of every iteration).
+// (More than 2^30 tickets are split over several launches: the kernel counts tickets in int.)
+static cudaError_t launch_iterations(Instance& in, bool cert, int64_t iters) {
   const LaunchPlan& pl = cert ? in.cert : in.fast;
-  SweepFn fr = get_sweep(in.d, pl.mode, pl.R, pl.ch, cert ? 4 : 0);
-  SweepFn fc = get_sweep(in.d, pl.mode, pl.R, pl.ch, cert ? 2 : 1);
+  SweepFn fn = get_sweep(in.d, pl.mode, pl.R, pl.ch, cert ? 1 : 0);
+  const int nitems = pl.n_row + pl.n_col;
+  const int64_t per_launch = std::max<int64_t>(1, ((int64_t)1 << 30) / nitems);
+  for (int64_t done = 0; done < iters;) {
+    const int64_t j = std::min(iters - done, per_launch);
+    // one iteration's items bound the useful CTAs: more would only wait for the next phase
+    const int grid = std::min(nitems, pl.resident);
+    const cudaError_t e = launch_sweep(fn, in.d_inst, pl.d_row, nitems, (int)j, grid, in.sched, in.stream);
+    if (e != cudaSuccess) return e;
+    done += j;
+  }
+  return cudaSuccess;
+}
+
+// A chunk: its fast iterations as one launch, then the certificate iteration (if any) as another;
+// in profiling mode an event before, between and after them (ev[0..2]).
+static cudaError_t issue_launches(Instance& in, int64_t count, bool cert_last, cudaEvent_t* ev) {
+  const int64_t nfast = count - (cert_last ? 1 : 0);
   cudaError_t e;
   if (ev && (e = cudaEventRecordWithFlags(ev[0], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-  e = launch_sweep(fr, in.d_inst, pl.d_row, pl.n_row, pl.grid_row, in.sched, in.stream);
-  if (e != cudaSuccess) return e;
+  if (nfast > 0 && (e = launch_iterations(in, false, nfast)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecordWithFlags(ev[1], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
-  e = launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.sched, in.stream);
-  if (e != cudaSuccess) return e;
+  if (cert_last && (e = launch_iterations(in, true, 1)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecordWithFlags(ev[2], in.stream, cudaEventRecordExternal)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
-// `count` iterations, the last one a certificate iteration if cert_last; replayed from a CUDA graph.
-// In profiling mode the graph also records an event between consecutive sweeps, and the chunk is
-// waited for so that the per-launch durations can be read.
+// `count` iterations, the last one a certificate iteration if cert_last: at most two launches,
+// replayed from a CUDA graph.  In profiling mode the graph also records events around them and the
+// chunk is waited for, so that the launch durations can be read.
 static ot_status issue_chunk(Context& ctx, Instance& in, int64_t count, bool cert_last) {
   if (count <= 0) return OT_OK;
   const bool prof = ctx.profile;
@@ -484,18 +501,16 @@ static ot_status issue_chunk(Context& ctx, Instance& in, int64_t count, bool cer
   if (prof) {
     evs = &in.graph_events[key];
     if (evs->empty()) {
-      evs->resize(2 * count + 1);
+      evs->resize(3);
       for (auto& e : *evs) OT_CUDA(cudaEventCreate(&e));
     }
   }
-  if (it == in.graphs.end() && in.use_graphs && count <= 4096) {
+  if (it == in.graphs.end() && in.use_graphs) {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     if (cudaStreamBeginCapture(in.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      cudaError_t e = cudaSuccess;
-      for (int64_t i = 0; i < count && e == cudaSuccess; ++i)
-        e = issue_iteration(in, cert_last && i == count - 1, prof ? evs->data() + 2 * i : nullptr);
-      cudaError_t e2 = cudaStreamEndCapture(in.stream, &g);
+      const cudaError_t e = issue_launches(in, count, cert_last, prof ? evs->data() : nullptr);
+      const cudaError_t e2 = cudaStreamEndCapture(in.stream, &g);
       if (e == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
         it = in.graphs.emplace(key, ge).first;
       }
@@ -506,24 +521,25 @@ static ot_status issue_chunk(Context& ctx, Instance& in, int64_t count, bool cer
   if (it != in.graphs.end()) {
     OT_CUDA(cudaGraphLaunch(it->second, in.stream));
   } else {
-    for (int64_t i = 0; i < count; ++i)
-      OT_CUDA(issue_iteration(in, cert_last && i == count - 1, prof ? evs->data() + 2 * i : nullptr));
+    OT_CUDA(issue_launches(in, count, cert_last, prof ? evs->data() : nullptr));
   }
+  const int64_t nfast = count - (cert_last ? 1 : 0);
   in.k += count;
-  ctx.launches += 2 * count;
+  ctx.launches += (nfast > 0 ? 1 : 0) + (cert_last ? 1 : 0);
   if (prof) {
     OT_CUDA(cudaStreamSynchronize(in.stream));
-    const double entries = (double)in.n * (double)in.m;
-    for (int64_t i = 0; i < count; ++i) {
-      const bool c = cert_last && i == count - 1;
-      float ms_r = 0, ms_c = 0;
-      OT_CUDA(cudaEventElapsedTime(&ms_r, (*evs)[2 * i], (*evs)[2 * i + 1]));
-      OT_CUDA(cudaEventElapsedTime(&ms_c, (*evs)[2 * i + 1], (*evs)[2 * i + 2]));
-      KernelStats& sr = ctx.stats[c ? 2 : 0];
-      KernelStats& sc = ctx.stats[c ? 3 : 1];
-      sr.launches += 1;
-      sr.entries += entries;
-      sr.ms += ms_r;
+    const double entries = 2.0 * (double)in.n * (double)in.m;  // row and column sweep
+    float ms_f = 0, ms_c = 0;
+    OT_CUDA(cudaEventElapsedTime(&ms_f, (*evs)[0], (*evs)[1]));
+    OT_CUDA(cudaEventElapsedTime(&ms_c, (*evs)[1], (*evs)[2]));
+    if (nfast > 0) {
+      KernelStats& sf = ctx.stats[0];
+      sf.launches += 1;
+      sf.entries += entries * (double)nfast;
+      sf.ms += ms_f;
+    }
+    if (cert_last) {
+      KernelStats& sc = ctx.stats[1];
       sc.launches += 1;
       sc.entries += entries;
       sc.ms += ms_c;
@@ -633,8 +649,8 @@ ot_status run_iterations(Context& ctx, Instance& in, int64_t n_iters, bool stop_
 
 ot_status standalone_certificate(Context& ctx, Instance& in) {
   const LaunchPlan& pl = in.cert;
-  SweepFn fc = get_sweep(in.d, pl.mode, pl.R, pl.ch, 3);
-  OT_CUDA(launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, pl.grid_col, in.sched, in.stream));
+  SweepFn fc = get_sweep(in.d, pl.mode, pl.R, pl.ch, 2);
+  OT_CUDA(launch_sweep(fc, in.d_inst, pl.d_col, pl.n_col, 1, std::min(pl.n_col, pl.resident), in.sched, in.stream));
   ctx.launches += 1;
   return read_ctrl(ctx, in);
 }
@@ -818,8 +834,10 @@ ot_status ot_state_set(ot_state* st, int which, const double* in_vec, int64_t k)
   size_t len = 0;
   double* p = vec_ptr(in, which, &len);
   OT_CUDA(cudaMemcpyAsync(p, in_vec, len * sizeof(double), cudaMemcpyHostToDevice, in.stream));
-  const long long kk = k;
-  OT_CUDA(cudaMemcpyAsync(in.h.k, &kk, sizeof(kk), cudaMemcpyHostToDevice, in.stream));
+  // k, the completed row sweeps and the next launch's starting k all become k
+  const long long kk[2] = {k, k};
+  OT_CUDA(cudaMemcpyAsync(in.h.k, &kk[0], sizeof(long long), cudaMemcpyHostToDevice, in.stream));
+  OT_CUDA(cudaMemcpyAsync(in.h.rows, kk, 2 * sizeof(long long), cudaMemcpyHostToDevice, in.stream));
   // the stored shift hints belong to the replaced state: mark both sides as missed, so the next
   // iteration runs without them and re-validates its own
   static const int kMissed[4] = {1, 1, 1, 1};
@@ -858,7 +876,7 @@ ot_status ot_launch_count(ot_context* ctx, int64_t* launches) {
 }
 
 ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* entries, double* ms) {
-  if (!ctx || kind < 0 || kind > 3) return OT_EINVAL;
+  if (!ctx || kind < 0 || kind > 1) return OT_EINVAL;
   const KernelStats& s = ctx->c.stats[kind];
   if (launches) *launches = s.launches;
   if (entries) *entries = s.entries;

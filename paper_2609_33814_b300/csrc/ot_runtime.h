@@ -11,7 +11,7 @@
 
 namespace ot {
 
-typedef void (*SweepFn)(const Inst*, const Item*, int, unsigned*);
+typedef void (*SweepFn)(const Inst*, const Item*, int, int, unsigned*);
 SweepFn get_sweep(int d, int mode, int R, int ch, int variant);
 
 // Accumulated timing of one kind of sweep launch (profiling mode).
@@ -24,7 +24,7 @@ struct KernelStats {
 struct Context {
   int device = 0;
   bool profile = false;
-  KernelStats stats[4];  // fast row, fast column, certificate row, certificate column
+  KernelStats stats[2];  // fast iterations, certificate iterations
   int64_t launches = 0;  // every kernel this context has launched (graph nodes included)
   uint32_t wait_limit = kWaitLimit;  // tile-wait bound given to the states created from now on
   int sms = 148;
@@ -45,10 +45,10 @@ struct LaunchPlan {
   int nms_row = 1, nms_col = 1;      // micro-splits of the reduced side (fixed per instance)
   int mst_row = 1, mst_col = 1;      // tiles per micro-split
   int group_row = 1, group_col = 1;  // micro-splits per work item when the instance runs alone
-  Item* d_row = nullptr;
+  Item* d_row = nullptr;              // the instance's items: row sweep, then (d_col) column sweep
   Item* d_col = nullptr;
   int n_row = 0, n_col = 0;
-  int grid_row = 0, grid_col = 0;
+  int resident = 0;                    // CTAs of the plan's kernel resident on the device
 };
 
 // Byte offsets of an instance's buffers inside its single device allocation.
@@ -100,14 +100,16 @@ ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q);
 void plan_launch(Context& ctx, const Instance& in, int mode, LaunchPlan& pl);
 void canonical_tile(int d, int mode, int* R, int* ch);
 int sweep_mode_of(int precision);
-void build_items(std::vector<Item>& out, int inst, int pblks, int nms, int group);
+void build_items(std::vector<Item>& out, int inst, int side, int pblks, int nms, int group);
 ot_status instance_init(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
 ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, const ot_params* q, cudaStream_t stream);
 ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p);
 ot_status read_ctrl(Context& ctx, Instance& in);
 ot_status absorb_cert(Context& ctx, Instance& in);
 void fill_result(const Instance& in, ot_result* r);
-cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int grid,
+// One launch of `iters` iterations over the instance table (nitems work items per iteration);
+// grid = CTAs (at most the resident count), sched = the stream's two-plus-one scheduler counters.
+cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int iters, int grid,
                          unsigned* sched, cudaStream_t stream);
 void instance_free(Instance& in);
 ot_status run_iterations(Context& ctx, Instance& in, int64_t n_iters, bool stop_rule, bool final_cert);

@@ -63,8 +63,8 @@ struct Lane {
   Item* d_items = nullptr;
   Item* h_items = nullptr;
   size_t items_cap = 0;
-  int off[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, grid[4] = {0, 0, 0, 0};
-  unsigned* d_sched = nullptr;         // work-item ticket counters of the lane's launches
+  int off[2] = {0, 0}, cnt[2] = {0, 0}, resident[2] = {0, 0};  // items per iteration of each kind
+  unsigned* d_sched = nullptr;         // scheduler counters of the lane's launches
   double entries_per_sweep = 0;        // sum of n * m over the active instances
   std::vector<cudaEvent_t> evs;        // profiling: one event between consecutive launches
   bool timed = false;                  // the last chunk recorded events
@@ -102,7 +102,7 @@ struct Server {
   void finish(Request* r, ot_status st);
 };
 
-static const int kMaxLaunch = 4;  // fast row, fast col, cert row, cert col
+static const int kMaxLaunch = 2;  // fast iterations, certificate iteration
 
 int Server::lane_for(const Request* r) {
   const int mode = sweep_mode_of(r->params.precision);
@@ -183,8 +183,8 @@ void Server::run_chunk(Lane& L) {
   if (L.dirty) {
     // instance table and work items of the four launch kinds for the current composition
     if (!L.d_sched) {
-      cudaMalloc(&L.d_sched, 2 * sizeof(unsigned));
-      cudaMemsetAsync(L.d_sched, 0, 2 * sizeof(unsigned), s);
+      cudaMalloc(&L.d_sched, 4 * sizeof(unsigned));
+      cudaMemsetAsync(L.d_sched, 0, 4 * sizeof(unsigned), s);
     }
     if (L.table_cap < na) {
       if (L.d_table) cudaFree(L.d_table);
@@ -195,46 +195,48 @@ void Server::run_chunk(Lane& L) {
     }
     for (size_t i = 0; i < na; ++i) L.h_table[i] = L.active[i]->inst->h;
     std::vector<Item> items;
-    const int Rs[4] = {L.R_fast, L.R_fast, L.R_cert, L.R_cert};
-    const int mode_of[4] = {L.mode, L.mode, L.cert_mode, L.cert_mode};
     for (int kind = 0; kind < kMaxLaunch; ++kind) {
-      const int R = Rs[kind];
-      const bool row = kind % 2 == 0;
-      SweepFn fn = get_sweep(L.d, mode_of[kind], R, kind < 2 ? L.ch_fast : 8, 0);
+      const bool cert = kind == 1;
+      SweepFn fn = get_sweep(L.d, cert ? L.cert_mode : L.mode, cert ? L.R_cert : L.R_fast, cert ? 8 : L.ch_fast,
+                             cert ? 1 : 0);
       const int resident = ctx.resident_ctas(fn);
-      // Each instance's micro-split layout is fixed (its numerics do not depend on the batch);
-      // the launch groups micro-splits into items of about equal size for this composition:
-      // roughly four waves of resident CTAs in total.
-      double tiles_total = 0;
-      for (size_t i = 0; i < na; ++i) {
-        const Instance& in = *L.active[i]->inst;
-        const LaunchPlan& pl = kind < 2 ? in.fast : in.cert;
-        const int64_t nq = row ? in.m : in.n;
-        tiles_total += (double)(row ? pl.pblk_row : pl.pblk_col) * (double)((nq + kTQ - 1) / kTQ);
-      }
-      const double target = std::max(1.0, tiles_total / (4.0 * resident));
+      L.resident[kind] = resident;
       L.off[kind] = (int)items.size();
-      for (size_t i = 0; i < na; ++i) {
-        const Instance& in = *L.active[i]->inst;
-        const LaunchPlan& pl = kind < 2 ? in.fast : in.cert;
-        const int nms = row ? pl.nms_row : pl.nms_col;
-        const int mst = row ? pl.mst_row : pl.mst_col;
-        const int group = std::max(1, std::min(nms, (int)std::lround(target / mst)));
-        build_items(items, (int)i, row ? pl.pblk_row : pl.pblk_col, nms, group);
+      for (int side = 0; side < 2; ++side) {
+        const bool row = side == 0;
+        // Each instance's micro-split layout is fixed (its numerics do not depend on the batch);
+        // the launch groups micro-splits into items of about equal size for this composition:
+        // roughly four waves of resident CTAs per sweep.
+        double tiles_total = 0;
+        for (size_t i = 0; i < na; ++i) {
+          const Instance& in = *L.active[i]->inst;
+          const LaunchPlan& pl = cert ? in.cert : in.fast;
+          const int64_t nq = row ? in.m : in.n;
+          tiles_total += (double)(row ? pl.pblk_row : pl.pblk_col) * (double)((nq + kTQ - 1) / kTQ);
+        }
+        const double target = std::max(1.0, tiles_total / (4.0 * resident));
+        const size_t first = items.size();
+        for (size_t i = 0; i < na; ++i) {
+          const Instance& in = *L.active[i]->inst;
+          const LaunchPlan& pl = cert ? in.cert : in.fast;
+          const int nms = row ? pl.nms_row : pl.nms_col;
+          const int mst = row ? pl.mst_row : pl.mst_col;
+          const int group = std::max(1, std::min(nms, (int)std::lround(target / mst)));
+          build_items(items, (int)i, side, row ? pl.pblk_row : pl.pblk_col, nms, group);
+        }
+        // longest items first within the sweep (the kernel hands them out in order)
+        auto work_of = [&](const Item& it) {
+          const Instance& in = *L.active[it.inst]->inst;
+          const LaunchPlan& pl = cert ? in.cert : in.fast;
+          const int64_t nq = row ? in.m : in.n;
+          const int qtiles = (int)((nq + kTQ - 1) / kTQ);
+          const int mst = row ? pl.mst_row : pl.mst_col;
+          return std::min(qtiles, (it.ms0 + it.nms) * mst) - it.ms0 * mst;
+        };
+        std::stable_sort(items.begin() + first, items.end(),
+                         [&](const Item& a, const Item& b) { return work_of(a) > work_of(b); });
       }
-      // longest items first: CTAs take items with a fixed stride, so this evens out their loads
-      auto work_of = [&](const Item& it) {
-        const Instance& in = *L.active[it.inst]->inst;
-        const LaunchPlan& pl = kind < 2 ? in.fast : in.cert;
-        const int64_t nq = row ? in.m : in.n;
-        const int qtiles = (int)((nq + kTQ - 1) / kTQ);
-        const int mst = row ? pl.mst_row : pl.mst_col;
-        return std::min(qtiles, (it.ms0 + it.nms) * mst) - it.ms0 * mst;
-      };
-      std::stable_sort(items.begin() + L.off[kind], items.end(),
-                       [&](const Item& a, const Item& b) { return work_of(a) > work_of(b); });
       L.cnt[kind] = (int)items.size() - L.off[kind];
-      L.grid[kind] = std::min(L.cnt[kind], resident);
     }
     if (L.items_cap < items.size()) {
       if (L.d_items) cudaFree(L.d_items);
@@ -250,23 +252,23 @@ void Server::run_chunk(Lane& L) {
     cudaMemcpyAsync(L.d_items, L.h_items, items.size() * sizeof(Item), cudaMemcpyHostToDevice, s);
     L.dirty = false;
   }
-  SweepFn fns[4] = {get_sweep(L.d, L.mode, L.R_fast, L.ch_fast, 0), get_sweep(L.d, L.mode, L.R_fast, L.ch_fast, 1),
-                    get_sweep(L.d, L.cert_mode, L.R_cert, 8, 4), get_sweep(L.d, L.cert_mode, L.R_cert, 8, 2)};
+  // the chunk: ce - 1 fast iterations as one launch, then the certificate iteration
+  SweepFn fns[2] = {get_sweep(L.d, L.mode, L.R_fast, L.ch_fast, 0), get_sweep(L.d, L.cert_mode, L.R_cert, 8, 1)};
+  const int iters[2] = {L.ce - 1, 1};
   L.timed = profile;
-  if (profile && L.evs.size() != (size_t)(2 * L.ce + 1)) {
+  if (profile && L.evs.size() != 3) {
     for (cudaEvent_t e : L.evs) cudaEventDestroy(e);
-    L.evs.assign(2 * L.ce + 1, nullptr);
+    L.evs.assign(3, nullptr);
     for (auto& e : L.evs) cudaEventCreate(&e);
   }
   if (profile) cudaEventRecord(L.evs[0], s);
-  for (int it = 0; it < L.ce; ++it) {
-    const bool cert = it == L.ce - 1;
-    for (int side = 0; side < 2; ++side) {
-      const int kind = (cert ? 2 : 0) + side;
-      launch_sweep(fns[kind], L.d_table, L.d_items + L.off[kind], L.cnt[kind], L.grid[kind], L.d_sched, s);
+  for (int kind = 0; kind < kMaxLaunch; ++kind) {
+    if (iters[kind] > 0) {
+      const int grid = std::min(L.cnt[kind], L.resident[kind]);  // one iteration's items bound the CTAs
+      launch_sweep(fns[kind], L.d_table, L.d_items + L.off[kind], L.cnt[kind], iters[kind], grid, L.d_sched, s);
       ctx.launches += 1;
-      if (profile) cudaEventRecord(L.evs[2 * it + side + 1], s);
     }
+    if (profile) cudaEventRecord(L.evs[kind + 1], s);
   }
   for (Request* r : L.active) {
     r->inst->k += L.ce;
@@ -406,15 +408,16 @@ void Server::loop() {
       Lane& L = lanes[i];
       if (!L.timed || L.active.empty()) continue;
       L.timed = false;
-      for (int it = 0; it < L.ce; ++it)
-        for (int side = 0; side < 2; ++side) {
-          float ms = 0;
-          cudaEventElapsedTime(&ms, L.evs[2 * it + side], L.evs[2 * it + side + 1]);
-          KernelStats& ks = ctx.stats[(it == L.ce - 1 ? 2 : 0) + side];
-          ks.launches += 1;
-          ks.entries += L.entries_per_sweep;
-          ks.ms += ms;
-        }
+      const int iters[2] = {L.ce - 1, 1};
+      for (int kind = 0; kind < kMaxLaunch; ++kind) {
+        if (iters[kind] <= 0) continue;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, L.evs[kind], L.evs[kind + 1]);
+        KernelStats& ks = ctx.stats[kind];
+        ks.launches += 1;
+        ks.entries += 2.0 * L.entries_per_sweep * iters[kind];  // row and column sweeps
+        ks.ms += ms;
+      }
     }
     std::vector<Request*> done_now;
     for (int i = 0; i < nl; ++i) retire(lanes[i], done_now);
@@ -686,7 +689,7 @@ ot_status ot_serve_profile_enable(ot_server* sv, int on) {
 }
 
 ot_status ot_serve_profile_read(ot_server* sv, int kind, int64_t* launches, double* entries, double* ms) {
-  if (!sv || kind < 0 || kind > 3) return OT_EINVAL;
+  if (!sv || kind < 0 || kind > 1) return OT_EINVAL;
   std::lock_guard<std::mutex> lk(sv->s.mu);
   const KernelStats& k = sv->s.ctx.stats[kind];
   if (launches) *launches = k.launches;

@@ -154,7 +154,6 @@ struct Acc<R, kSweepF64, false> {
 //          all pairs / a quarter of the pairs
 //          kSweepComp: exponent in float-float (error-free transforms), MUFU exp2, Kahan sums
 //          kSweepF64 : exponent, exp2 and sums in FP64
-//   SIDE   0 = row sweep (Algorithm 1 row update), 1 = column sweep (column update)
 //   CERT   column sweep also accumulates N_q = sum_p ||u-w||^2 E_pq (Algorithm 2)
 //   UPDATE false: standalone certificate of the current state, no state update
 // ---------------------------------------------------------------------------------------------
@@ -165,17 +164,22 @@ constexpr int sweep_min_blocks() {
   return !is_fast_mode(MODE) ? 1 : (R * D <= 4 ? 5 : (R * D <= 12 ? 3 : 1));
 }
 
-// Work distribution: items are handed out in index order (the host sorts them longest first) from
-// the ticket counter sched[0]; sched[1] counts CTAs that have finished, and the last one resets
-// both, so consecutive launches on a stream can share the two counters.
-template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
+// One launch runs `iters` iterations of every instance in the table: ticket t is work item
+// t % nitems of the launch's iteration t / nitems, and the host lists each iteration's row items
+// before its column items, each group longest first.  Tickets are handed out in order from
+// sched[0]; an update item waits until its instance has finished the previous phase (the column
+// sweep of the previous iteration for a row item, the row sweep of the same iteration for a column
+// item).  A CTA only waits while it holds no unfinished item, and every ticket it waits on is
+// smaller than its own and held by a running CTA, so the launch needs no co-residency.  sched[1]
+// counts CTAs that have finished and the last one resets sched[0..2]; sched[2] is set when a CTA
+// gives up, so that waiting CTAs stop too.
+template <int D, int R, int MODE, bool CERT, bool UPDATE, int CHF>
 __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) sweep_kernel(const Inst* __restrict__ insts,
-                                                         const Item* __restrict__ items, int nitems,
+                                                         const Item* __restrict__ items, int nitems, int iters,
                                                          unsigned* __restrict__ sched) {
   static_assert(!(CERT && is_fast_mode(MODE)), "certificate sweeps use the compensated or FP64 mode");
   constexpr bool FAST = is_fast_mode(MODE);
-  static_assert(UPDATE || (CERT && SIDE == 1), "a non-updating sweep is the standalone certificate");
-  constexpr bool ACCN = CERT && SIDE == 1;  // accumulate N_q (Algorithm 2) on the column sweep
+  static_assert(UPDATE || CERT, "a non-updating sweep is the standalone certificate");
   typedef typename PartT<MODE>::type Part;
   constexpr uint32_t kPackTileBytes = kNComp * kTQ * 4;  // one pack tile, all components
   constexpr int kStageFloats = kStageTiles * kNComp * kTQ;
@@ -186,7 +190,10 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   __shared__ __align__(8) uint64_t bars[kStages];
   __shared__ double red[kThreads];
   __shared__ int s_flag;
-  __shared__ int s_ring[8];  // item indices in the order the producer took them (<= kStages + 1 ahead)
+  __shared__ int s_abort;
+  __shared__ long long s_kit[2];  // per item (double-buffered by item parity): iteration k
+  __shared__ int s_tk[2];         // and ticket
+  __shared__ int s_ring[8];  // tickets in the order the producer took them (<= kStages + 1 ahead)
 
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -196,64 +203,126 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   }
   __syncthreads();
 
-  // The TMA pipeline runs across work items: thread 0 keeps kStages stages in flight, taking the
-  // CTA's next item from the ticket counter before the current one ends, so it never drains.  The
-  // item index reaches the other threads through s_ring: it is written before the stage that
-  // needs it is issued, hence before a CTA barrier that every consumer of that item passes.
-  uint32_t gcons = 0;  // stages consumed by this CTA (stage slot and mbarrier parity)
-  uint32_t gprod = 0;  // stages issued by this CTA
-  uint32_t pseq = 0;   // items taken by this CTA
-  int pr_it = 0, pr_us = 0, pr_nst = 0, pr_qt0 = 0, pr_ntl = 0;
-  const float* pr_qpack = nullptr;
-  auto pr_load = [&]() {
-    pr_it = (int)atomicAdd(&sched[0], 1u);
-    s_ring[pseq++ & 7u] = pr_it;
-    if (pr_it >= nitems) return;
-    const Item itp = items[pr_it];
-    const Inst* Ip = insts + itp.inst;
-    const int qtl = SIDE == 0 ? Ip->tiles_y : Ip->tiles_x;
-    const int mstp = Ip->ms_tiles[CERT ? 1 : 0][SIDE];
-    pr_qt0 = itp.ms0 * mstp;
-    pr_ntl = min(qtl, (itp.ms0 + itp.nms) * mstp) - pr_qt0;
-    pr_nst = (pr_ntl + kStageTiles - 1) / kStageTiles;
-    pr_qpack = SIDE == 0 ? Ip->ypack : Ip->xpack;
-    pr_us = 0;
+  const int total = nitems * iters;
+  // has the instance finished the phase that ticket (item it, launch iteration j) depends on?
+  // (k0 does not change while the instance still has items in this launch)
+  auto dep_met = [&](const Item& it, int j) -> bool {
+    if constexpr (!UPDATE) return true;  // the standalone certificate reads a finished state
+    const Inst* Ip = insts + it.inst;
+    const long long need = __ldcg(Ip->k0) + j;
+    return it.side == 0 ? ld_acquire(Ip->k) >= need : ld_acquire(Ip->rows) >= need + 1;
   };
-  auto produce = [&]() {
-    if (pr_it >= nitems) return;
-    const int stg = gprod % kStages;
-    const int tiles = min(kStageTiles, pr_ntl - pr_us * kStageTiles);
-    mbar_expect_tx(&bars[stg], tiles * kPackTileBytes);
-    bulk_g2s(smem + stg * kStageFloats, pr_qpack + (size_t)(pr_qt0 + pr_us * kStageTiles) * kNComp * kTQ,
-             tiles * kPackTileBytes, &bars[stg]);
-    ++gprod;
-    if (++pr_us == pr_nst) pr_load();
+
+  // The TMA pipeline runs across work items: thread 0 keeps up to kStages stages in flight, taking
+  // the CTA's next ticket before the current item ends.  It stops at an item whose dependency is
+  // not met yet (re-checking whenever it is called) and never waits itself.  The ticket reaches the
+  // other threads through s_ring: it is written before any stage of its item is issued and before a
+  // CTA barrier that every consumer of the item passes.
+  // producer state: used by thread 0 only, kept in shared memory to spare every thread's registers
+  struct Producer {
+    const float* qpack;
+    Item item;
+    uint32_t gprod, pseq, seq;  // stages issued, tickets taken, sequence number of the current one
+    int t, j, us, nst, qt0, ntl;
+    bool ok;                    // the current item may be issued (dependency met)
+  };
+  __shared__ Producer ps;
+  uint32_t gcons = 0;  // stages consumed by this CTA (stage slot and mbarrier parity)
+  auto pr_next = [&]() {
+    ps.t = (int)atomicAdd(&sched[0], 1u);
+    ps.seq = ps.pseq++;
+    s_ring[ps.seq & 7u] = ps.t;
+    ps.ok = false;
+    if (ps.t >= total) return;
+    const Item it = items[ps.t % nitems];
+    ps.item = it;
+    ps.j = ps.t / nitems;
+    const Inst* Ip = insts + it.inst;
+    const int qtl = it.side == 0 ? Ip->tiles_y : Ip->tiles_x;
+    const int mstp = Ip->ms_tiles[CERT ? 1 : 0][it.side];
+    ps.qt0 = it.ms0 * mstp;
+    ps.ntl = min(qtl, (it.ms0 + it.nms) * mstp) - ps.qt0;
+    ps.nst = (ps.ntl + kStageTiles - 1) / kStageTiles;
+    ps.qpack = it.side == 0 ? Ip->ypack : Ip->xpack;
+    ps.us = 0;
+  };
+  auto pr_ready = [&]() -> bool {
+    if (ps.t >= total) return false;
+    if (!ps.ok) {
+      if (!dep_met(ps.item, ps.j)) return false;
+      fence_proxy_async_global();
+      ps.ok = true;
+    }
+    return true;
+  };
+  // issue stages until kStages are in flight beyond the `consumed` ones, or the producer stops
+  auto refill = [&](uint32_t consumed) {
+    while (ps.gprod - consumed < (uint32_t)kStages && pr_ready()) {
+      const int stg = ps.gprod % kStages;
+      const int tiles = min(kStageTiles, ps.ntl - ps.us * kStageTiles);
+      mbar_expect_tx(&bars[stg], tiles * kPackTileBytes);
+      bulk_g2s(smem + stg * kStageFloats, ps.qpack + (size_t)(ps.qt0 + ps.us * kStageTiles) * kNComp * kTQ,
+               tiles * kPackTileBytes, &bars[stg]);
+      ++ps.gprod;
+      if (++ps.us == ps.nst) pr_next();
+    }
   };
   if (tid == 0) {
-    pr_load();
-    for (int j = 0; j < kStages; ++j) produce();
+    ps.gprod = 0;
+    ps.pseq = 0;
+    pr_next();
+    refill(0);
   }
   __syncthreads();
 
   bool aborted = false;
   for (uint32_t cseq = 0;; ++cseq) {
-    const int it = s_ring[cseq & 7u];
-    if (it >= nitems) break;
-    const Item item = items[it];
+    // If the producer stopped at this very item, wait here for its dependency (the CTA holds no
+    // unfinished item now), then start its stages.  Thread 0 also publishes the item's iteration.
+    if (tid == 0) {
+      s_abort = 0;
+      const int t = s_ring[cseq & 7u];
+      if (ps.seq == cseq && t < total && !ps.ok) {
+        const Inst* Ip = insts + ps.item.inst;
+        uint32_t polls = 0;
+        while (!dep_met(ps.item, ps.j)) {
+          if (polls++ >= Ip->wait_limit || *(volatile unsigned*)&sched[2] != 0u) {
+            atomicOr(Ip->err, kErrTimeout);
+            atomicExch(&sched[2], 1u);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(256);
+        }
+        if (!s_abort) {
+          fence_proxy_async_global();
+          ps.ok = true;
+          refill(gcons);
+        }
+      }
+      s_tk[cseq & 1u] = t;
+      if (t < total && !s_abort) s_kit[cseq & 1u] = ld_acquire(insts[items[t % nitems].inst].k) - (UPDATE ? 0 : 1);
+    }
+    __syncthreads();
+    if (s_abort) {
+      aborted = true;
+      break;
+    }
+    if (s_tk[cseq & 1u] >= total) break;
+    {  // ---- the item's sweep (its locals end here; the epilogue re-derives what it needs) ----
+    const Item item = items[s_tk[cseq & 1u] % nitems];
+    const int side = item.side;
+    const bool accn = CERT && side == 1;  // accumulate N_q (Algorithm 2) on the column sweep
     const Inst* __restrict__ I = insts + item.inst;
-    const int np = SIDE == 0 ? I->n : I->m;
-    const int qtiles = SIDE == 0 ? I->tiles_y : I->tiles_x;
-    const int splits = I->nms[CERT ? 1 : 0][SIDE];      // partials per point (all micro-splits)
-    const int mst = I->ms_tiles[CERT ? 1 : 0][SIDE];    // tiles per micro-split
-    const int pblks = (np + kThreads * R - 1) / (kThreads * R);
-    const float* __restrict__ ppack = SIDE == 0 ? I->xpack : I->ypack;
+    const int np = side == 0 ? I->n : I->m;
+    const int qtiles = side == 0 ? I->tiles_y : I->tiles_x;
+    const int mst = I->ms_tiles[CERT ? 1 : 0][side];    // tiles per micro-split
+    const float* __restrict__ ppack = side == 0 ? I->xpack : I->ypack;
     const int qt0 = item.ms0 * mst;
     const int qt1 = min(qtiles, (item.ms0 + item.nms) * mst);
     const int ntl = qt1 - qt0;
-    const long long kiter = *I->k - (UPDATE ? 0 : 1);
-    const double eps = eps_of(I, kiter);
-    const double inv_eps = 1.0 / eps;
-    const double sig = 2.0 * I->kappa * kLog2e * inv_eps;
+    const long long kiter = s_kit[cseq & 1u];
+    const double sig = 2.0 * I->kappa * kLog2e / eps_of(I, kiter);
 
     // ---- thread-side points ----
     float u[R][D];
@@ -320,11 +389,11 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     float hs[R];
     bool use_hint = false;
     if constexpr (FAST) {
-      use_hint = kiter >= 1 && I->hint_bad != nullptr && __ldcg(&I->hint_bad[2 * SIDE + ((kiter - 1) & 1)]) == 0;
+      use_hint = kiter >= 1 && I->hint_bad != nullptr && __ldcg(&I->hint_bad[2 * side + ((kiter - 1) & 1)]) == 0;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
-        hs[r] = (use_hint && p < np) ? floorf(__ldcg(&I->hint[SIDE][p])) - kHintMargin : -INFINITY;
+        hs[r] = (use_hint && p < np) ? floorf(__ldcg(&I->hint[side][p])) - kHintMargin : -INFINITY;
       }
     }
 
@@ -556,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           for (int cc = 0; cc < CH; ++cc) {
             const int c = c0 + cc;
             float w[D];
-            if constexpr (ACCN) {
+            if (accn) {
 #pragma unroll
               for (int k = 0; k < D; ++k) w[k] = S[k * kTQ + c];
             }
@@ -566,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
               if constexpr (MODE == kSweepF64) E = exp2(v[r][cc]);
               else E = ex2_mufu(v[r][cc]);
               cs[r] += E;
-              if constexpr (ACCN) {
+              if (accn) {
                 V d2 = 0;
 #pragma unroll
                 for (int k = 0; k < D; ++k) {
@@ -584,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
               st.n[r] += cn[r];
             } else {
               kahan_add(st.s[r], st.kc[r], cs[r]);
-              if constexpr (ACCN) kahan_add(st.n[r], st.nc[r], cn[r]);
+              if (accn) kahan_add(st.n[r], st.nc[r], cn[r]);
             }
           }
         }
@@ -603,20 +672,33 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       if (!all_ok) {
         if (tid == 0) {
           atomicOr(I->err, kErrTimeout);
+          atomicExch(&sched[2], 1u);  // stop CTAs that wait for a phase this CTA will not finish
           // let every copy still in flight (the stage that timed out included) land before the
           // CTA's shared memory is released; waits on a completed phase return at once
-          for (uint32_t gj = g; gj < gprod; ++gj)
+          for (uint32_t gj = g; gj < ps.gprod; ++gj)
             mbar_wait_bounded(&bars[gj % kStages], (gj / kStages) & 1u, kWaitLimit);
         }
         aborted = true;
         break;
       }
-      if (tid == 0) produce();  // refill the slot just consumed (possibly with the next item's tiles)
+      if (tid == 0) refill(g + 1);  // refill the slot just consumed (possibly with later items' tiles)
     }
     if (aborted) break;
     gcons += nst;
+    }
 
     // ---- last CTA of this point block runs the epilogue ----
+    const int tk = s_tk[cseq & 1u];
+    const int jit = tk / nitems;  // iteration of this launch the item belongs to
+    const Item item = items[tk % nitems];
+    const int side = item.side;
+    const Inst* __restrict__ I = insts + item.inst;
+    const int np = side == 0 ? I->n : I->m;
+    const int splits = I->nms[CERT ? 1 : 0][side];  // partials per point (all micro-splits)
+    const int pblks = (np + kThreads * R - 1) / (kThreads * R);
+    const long long kiter = s_kit[cseq & 1u];
+    const bool accn = CERT && side == 1;
+    const Part* part = reinterpret_cast<const Part*>(I->part);
     __threadfence();
     __syncthreads();
     if (tid == 0)
@@ -625,13 +707,17 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     if (!s_flag) continue;
     __threadfence();
 
+    const double eps = eps_of(I, kiter);
+    const double inv_eps = 1.0 / eps;
+    const bool use_hint = FAST && kiter >= 1 && I->hint_bad != nullptr &&
+                          __ldcg(&I->hint_bad[2 * side + ((kiter - 1) & 1)]) == 0;
     const double lam = I->lambda;
     const double inv_lam = 1.0 / lam;
     const double inv_eps1 = 1.0 / eps_of(I, kiter + 1);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     bool bad = false;
     bool hmiss = false;  // a stored hint missed this sweep's log-sum-exp by more than kHintTol
-    float* const hint = UPDATE ? I->hint[SIDE] : nullptr;
+    float* const hint = UPDATE ? I->hint[side] : nullptr;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
@@ -688,11 +774,11 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
               Nc *= f;
               mxf = ms;
               kahan_add(Sf, Sc, pr[u].y);
-              if constexpr (ACCN) kahan_add(Nf, Nc, pr[u].z);
+              if (accn) kahan_add(Nf, Nc, pr[u].z);
             } else {
               const float f = exp2_neg_int(mxf - ms);
               kahan_add(Sf, Sc, pr[u].y * f);
-              if constexpr (ACCN) kahan_add(Nf, Nc, pr[u].z * f);
+              if (accn) kahan_add(Nf, Nc, pr[u].z * f);
             }
           }
         }
@@ -713,12 +799,13 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         bad |= use_hint && e - l > kHintGuard;  // flushed terms could matter: reject the sweep
         hint[p] = (float)(lse2 * eps * inv_eps1);
       }
-      if constexpr (SIDE == 0) {
+      // state written by other CTAs of this launch (earlier phases) is read through L2
+      if (side == 0) {
         const double lse = lse2 * kLn2 - I->xn2[p] * inv_eps;
         const double lah = I->log_a[p] - lse;
         bad |= !isfinite(lah);
         I->log_alpha_hat[p] = lah;
-        I->log_alpha[p] = (1.0 - lam) * I->log_alpha[p] + lam * lah;
+        I->log_alpha[p] = (1.0 - lam) * __ldcg(&I->log_alpha[p]) + lam * lah;
         store_h(I->xpack, p, I->d, (lah - I->xn2[p] * inv_eps) * kLog2e);
         if constexpr (CERT) {
           const double f = eps * lah;
@@ -732,9 +819,9 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         if constexpr (UPDATE) {
           lbh = I->log_b[p] - lse;
           bad |= !isfinite(lbh);
-          t = I->log_beta_tilde_next[p];
+          t = __ldcg(&I->log_beta_tilde_next[p]);
           I->log_beta_tilde[p] = t;
-          const double bold = I->log_beta[p];
+          const double bold = __ldcg(&I->log_beta[p]);
           const double bnew = (1.0 - lam) * bold + lam * lbh;
           I->log_beta_prev[p] = bold;
           I->log_beta[p] = bnew;
@@ -743,8 +830,8 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           I->log_beta_tilde_next[p] = tn;
           store_h(I->ypack, p, I->d, (tn - I->yn2[p] * inv_eps1) * kLog2e);
         } else {
-          lbh = I->log_beta_hat[p];
-          t = I->log_beta_tilde[p];
+          lbh = __ldcg(&I->log_beta_hat[p]);
+          t = __ldcg(&I->log_beta_tilde[p]);
         }
         if constexpr (CERT) {
           const double sj = exp(t + lse);
@@ -759,10 +846,10 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     }
     if (bad) atomicOr(I->err, kErrNonFinite);
     if (hint != nullptr && __syncthreads_or(hmiss ? 1 : 0) && tid == 0)
-      atomicAdd(&I->hint_bad[2 * SIDE + (kiter & 1)], 1);
+      atomicAdd(&I->hint_bad[2 * side + (kiter & 1)], 1);
     if constexpr (CERT) {
       const double s0 = block_sum(acc0, red);
-      if constexpr (SIDE == 0) {
+      if (side == 0) {
         if (tid == 0) I->blk[item.pblk] = s0;
       } else {
         const double s1 = block_sum(acc1, red);
@@ -777,63 +864,76 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     }
     if (tid == 0) I->cnt[item.pblk] = 0u;
 
-    if constexpr (SIDE == 1) {
-      // ---- last point block of the instance: advance k, finish the certificate ----
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) s_flag = (atomicAdd(I->done, 1u) == (unsigned)(pblks - 1));
-      __syncthreads();
-      if (!s_flag) continue;
-      __threadfence();
-      if constexpr (CERT) {
-        double rf;
-        if constexpr (UPDATE) {
-          double v = 0.0;
-          for (int b = tid; b < I->pblk_x; b += kThreads) v += __ldcg(&I->blk[b]);
-          rf = block_sum(v, red);
-        } else {
-          // standalone certificate: <r, f> with f = eps log alpha-hat from the state
-          double v = 0.0;
-          for (int i = tid; i < I->n; i += kThreads) {
-            const double f = eps * I->log_alpha_hat[i];
-            I->f_cur[i] = f;
-            v += I->a[i] * f;
-          }
-          rf = block_sum(v, red);
-        }
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-        for (int b = tid; b < pblks; b += kThreads) {
-          const double* bb = I->blk + I->pblk_x + 3 * b;
-          v0 += __ldcg(&bb[0]);
-          v1 += __ldcg(&bb[1]);
-          v2 += __ldcg(&bb[2]);
-        }
-        const double cg = block_sum(v0, red);
-        const double smu = block_sum(v1, red);
-        const double dab = block_sum(v2, red);
+    // ---- last point block of the instance's phase ----
+    fence_proxy_async_global();  // the packed h just written is read by bulk copies of a later phase
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_flag = (atomicAdd(I->done, 1u) == (unsigned)(pblks - 1));
+    __syncthreads();
+    if (!s_flag) continue;
+    __threadfence();
+    if (side == 0) {
+      // row sweep complete: release the instance's column sweep of this iteration
+      if constexpr (UPDATE) {
         if (tid == 0) {
-          const double delta = 0.5 * dab;
-          double* cr = I->cert;
-          cr[kCertIter] = (double)kiter;
-          cr[kCertEps] = eps;
-          cr[kCertU] = smu + I->omega * delta;
-          cr[kCertL] = rf + cg;
-          cr[kCertDelta] = delta;
-          cr[kCertCostZ] = smu;
-          cr[kCertRF] = rf;
-          cr[kCertCG] = cg;
+          *I->done = 0u;
+          __threadfence();
+          st_release(I->rows, kiter + 1);
         }
       }
-      if (tid == 0) {
-        if constexpr (UPDATE) {
-          *I->k = kiter + 1;
-          // the counters iteration kiter + 1 fills (last read by iteration kiter)
-          if (I->hint_bad != nullptr) {
-            I->hint_bad[(kiter + 1) & 1] = 0;
-            I->hint_bad[2 + ((kiter + 1) & 1)] = 0;
-          }
+      continue;
+    }
+    // column sweep complete: finish the certificate, advance k (releasing the next iteration)
+    if constexpr (CERT) {
+      double rf;
+      if constexpr (UPDATE) {
+        double v = 0.0;
+        for (int b = tid; b < I->pblk_x; b += kThreads) v += __ldcg(&I->blk[b]);
+        rf = block_sum(v, red);
+      } else {
+        // standalone certificate: <r, f> with f = eps log alpha-hat from the state
+        double v = 0.0;
+        for (int i = tid; i < I->n; i += kThreads) {
+          const double f = eps * __ldcg(&I->log_alpha_hat[i]);
+          I->f_cur[i] = f;
+          v += I->a[i] * f;
         }
-        *I->done = 0u;
+        rf = block_sum(v, red);
+      }
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+      for (int b = tid; b < pblks; b += kThreads) {
+        const double* bb = I->blk + I->pblk_x + 3 * b;
+        v0 += __ldcg(&bb[0]);
+        v1 += __ldcg(&bb[1]);
+        v2 += __ldcg(&bb[2]);
+      }
+      const double cg = block_sum(v0, red);
+      const double smu = block_sum(v1, red);
+      const double dab = block_sum(v2, red);
+      if (tid == 0) {
+        const double delta = 0.5 * dab;
+        double* cr = I->cert;
+        cr[kCertIter] = (double)kiter;
+        cr[kCertEps] = eps;
+        cr[kCertU] = smu + I->omega * delta;
+        cr[kCertL] = rf + cg;
+        cr[kCertDelta] = delta;
+        cr[kCertCostZ] = smu;
+        cr[kCertRF] = rf;
+        cr[kCertCG] = cg;
+      }
+    }
+    if (tid == 0) {
+      *I->done = 0u;
+      if constexpr (UPDATE) {
+        // the hint-miss counters iteration kiter + 1 fills (last read by iteration kiter)
+        if (I->hint_bad != nullptr) {
+          I->hint_bad[(kiter + 1) & 1] = 0;
+          I->hint_bad[2 + ((kiter + 1) & 1)] = 0;
+        }
+        if (jit == iters - 1) *I->k0 = kiter + 1;  // the next launch starts here
+        __threadfence();
+        st_release(I->k, kiter + 1);
       }
     }
   }
@@ -842,35 +942,33 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     __threadfence();
     if (atomicAdd(&sched[1], 1u) == gridDim.x - 1) {
       sched[0] = 0u;
+      sched[2] = 0u;
+      __threadfence();
       sched[1] = 0u;
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Launch table: one entry per instantiated (D, R, MODE, SIDE, CERT, UPDATE).
+// Launch table: one entry per instantiated (D, R, MODE, CERT, UPDATE, chunk).
 // ---------------------------------------------------------------------------------------------
-typedef void (*SweepFn)(const Inst*, const Item*, int, unsigned*);
+typedef void (*SweepFn)(const Inst*, const Item*, int, int, unsigned*);
 
-template <int D, int R, int MODE, int SIDE, bool CERT, bool UPDATE, int CHF>
+template <int D, int R, int MODE, bool CERT, bool UPDATE, int CHF>
 static SweepFn sweep_ptr() {
-  return &sweep_kernel<D, R, MODE, SIDE, CERT, UPDATE, CHF>;
+  return &sweep_kernel<D, R, MODE, CERT, UPDATE, CHF>;
 }
 
-// variant index: 0 row, 1 col, 2 col + certificate, 3 standalone certificate, 4 row + certificate
+// variant index: 0 fast iterations, 1 certificate iterations, 2 standalone certificate
 template <int D, int R, int MODE, int CHF>
 static SweepFn sweep_variant(int v) {
   switch (v) {
-    case 0: return sweep_ptr<D, R, MODE, 0, false, true, CHF>();
-    case 1: return sweep_ptr<D, R, MODE, 1, false, true, CHF>();
+    case 0: return sweep_ptr<D, R, MODE, false, true, CHF>();
+    case 1:
+      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, true, true, CHF>();
+      return nullptr;
     case 2:
-      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, 1, true, true, CHF>();
-      return nullptr;
-    case 3:
-      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, 1, true, false, CHF>();
-      return nullptr;
-    case 4:
-      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, 0, true, true, CHF>();
+      if constexpr (!is_fast_mode(MODE)) return sweep_ptr<D, R, MODE, true, false, CHF>();
       return nullptr;
   }
   return nullptr;
