@@ -274,6 +274,12 @@ ot_status ot_launch_count(ot_context* ctx, int64_t* launches);
  * nout >= 12; iters >= 1 sets the loop length (10^4 .. 10^5 is typical). */
 ot_status ot_probe_pipes(int device, int iters, double* out, int nout);
 
+/* exp2 of n host floats x by the fast sweep's methods, into n host floats out: method 0 the SFU's
+ * ex2.approx.ftz, method 1 the FMA-pipe polynomial of OT_EXP_POLY / OT_EXP_SPLIT (x = round(x) + f,
+ * a degree-5 minimax polynomial for 2^f on [-1/2, 1/2], x clamped to [-125, 126]).  Allocates and
+ * frees its own device buffers on `device`; returns OT_EINVAL for other methods or n < 1. */
+ot_status ot_probe_exp2(int device, int method, const float* x, float* out, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

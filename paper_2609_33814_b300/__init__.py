@@ -109,6 +109,7 @@ _lib.ot_profile_read.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.
 _lib.ot_launch_count.argtypes = [_P, C.POINTER(C.c_int64)]
 _lib.ot_debug_set_wait_limit.argtypes = [_P, C.c_uint32]
 _lib.ot_probe_pipes.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int]
+_lib.ot_probe_exp2.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64]
 
 
 class OTError(RuntimeError):
@@ -359,3 +360,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def probe_exp2(x, method: str = "poly", device: int = 0) -> np.ndarray:
+    """exp2 of the float32 array x by the sweep's SFU ("mufu") or FMA-pipe polynomial ("poly")."""
+    xs = np.ascontiguousarray(x, np.float32)
+    out = np.empty_like(xs)
+    st = _lib.ot_probe_exp2(int(device), {"mufu": 0, "poly": 1}[method], xs.ctypes.data, out.ctypes.data,
+                            int(xs.size))
+    if st != OT_OK:
+        raise OTError(st, "ot_probe_exp2")
+    return out

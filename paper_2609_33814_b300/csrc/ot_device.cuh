@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "ot_exp2_poly.cuh"
+
 namespace ot {
 
 typedef unsigned long long u64;
@@ -128,6 +130,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// 2^x for a pair, on the FP32/INT pipes: x = n + f with n = round(x) (magic-number rounding),
+// 2^f by the fitted polynomial (|f| <= 1/2), 2^n added into the exponent bits.  x is clamped to
+// [-125, 126] so the result stays a normal float (an overflow still shows up as a huge value).
+__device__ __forceinline__ u64 exp2_poly2(u64 v) {
+  float lo, hi;
+  up2(v, lo, hi);
+  lo = fminf(fmaxf(lo, -125.0f), 126.0f);
+  hi = fminf(fmaxf(hi, -125.0f), 126.0f);
+  const u64 x = pk2(lo, hi);
+  const u64 magic = pk2(12582912.0f, 12582912.0f);  // 1.5 * 2^23
+  const u64 t = add2(x, magic);
+  const u64 f = sub2(x, sub2(t, magic));
+  u64 p = fma2(pk2(kExp2Poly[5], kExp2Poly[5]), f, pk2(kExp2Poly[4], kExp2Poly[4]));
+  p = fma2(p, f, pk2(kExp2Poly[3], kExp2Poly[3]));
+  p = fma2(p, f, pk2(kExp2Poly[2], kExp2Poly[2]));
+  p = fma2(p, f, pk2(kExp2Poly[1], kExp2Poly[1]));
+  p = fma2(p, f, pk2(kExp2Poly[0], kExp2Poly[0]));
+  float t0, t1, p0, p1;
+  up2(t, t0, t1);
+  up2(p, p0, p1);
+  p0 = __int_as_float(__float_as_int(p0) + (__float_as_int(t0) << 23));
+  p1 = __int_as_float(__float_as_int(p1) + (__float_as_int(t1) << 23));
+  return pk2(p0, p1);
 }
 
 }  // namespace ot

@@ -113,3 +113,45 @@ extern "C" ot_status ot_probe_pipes(int device, int iters, double* out, int nout
   cudaFree(d_out);
   return st;
 }
+
+namespace ot {
+// exp2 of each input by the method the fast sweeps use: MUFU ex2.approx.ftz (method 0) or the
+// FMA-pipe polynomial (method 1), two lanes at a time as in the sweep.
+__global__ void exp2_probe_kernel(const float* __restrict__ x, float* __restrict__ y, int64_t n, int method) {
+  const int64_t i = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= n) return;
+  const float a = x[i], b = i + 1 < n ? x[i + 1] : 0.0f;
+  float ra, rb;
+  if (method == 0) {
+    ra = ex2_mufu(a);
+    rb = ex2_mufu(b);
+  } else {
+    up2(exp2_poly2(pk2(a, b)), ra, rb);
+  }
+  y[i] = ra;
+  if (i + 1 < n) y[i + 1] = rb;
+}
+}  // namespace ot
+
+extern "C" ot_status ot_probe_exp2(int device, int method, const float* x, float* out, int64_t n) {
+  using namespace ot;
+  if (!x || !out || n < 1 || (method != 0 && method != 1)) return OT_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return OT_ECUDA;
+  float *dx = nullptr, *dy = nullptr;
+  if (cudaMalloc(&dx, n * sizeof(float)) != cudaSuccess) return OT_ENOMEM;
+  if (cudaMalloc(&dy, n * sizeof(float)) != cudaSuccess) {
+    cudaFree(dx);
+    return OT_ENOMEM;
+  }
+  ot_status st = OT_OK;
+  const int64_t pairs = (n + 1) / 2;
+  if (cudaMemcpy(dx, x, n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) st = OT_ECUDA;
+  if (st == OT_OK) {
+    exp2_probe_kernel<<<(unsigned)((pairs + 255) / 256), 256>>>(dx, dy, n, method);
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpy(out, dy, n * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = OT_ECUDA;
+  }
+  cudaFree(dx);
+  cudaFree(dy);
+  return st;
+}

@@ -90,3 +90,40 @@ def test_large_colour_transfer_size_sampled_rows(ctx):
     err = np.abs(eta * (lah[rows] - ref)).max() / np.abs(eta * ref).max()
     assert err <= 1e-5, err
     S.close()
+
+
+def test_translation_bound_at_colour_transfer_size(ctx):
+    """p* between a measure and its translate is kappa ||v||^2 at any size (the optimal plan is the
+    translation), so the certificate must bracket it: L_best <= p* <= U_best at 2^20 points, d = 3.
+    Colours are quantised to multiples of 2^-10 and v too, so y = x + v is exact in float32."""
+    n = 1 << 20
+    x = np.round(I.rgb_cloud(n, seed=11).astype(np.float64) * 1024.0) / 1024.0
+    v = np.array([52.0, -31.0, 17.0]) / 1024.0
+    y = x + v
+    a = np.full(n, 1.0 / n)
+    kappa = 1.0 / 3.0
+    pstar = O.pstar_translation(v, kappa)
+    f, g, res = ctx.solve(x.astype(np.float32), y.astype(np.float32), a, a, cost_scale=kappa, omega=0.0,
+                          eps0=0.1, lam=1.0, max_iters=20, cert_every=10)
+    assert res["n_certs"] == 2
+    assert res["L_best"] <= pstar + 1e-12 and pstar <= res["U_best"] + 1e-12, (res["L_best"], pstar, res["U_best"])
+
+
+def test_one_dimensional_monotone_bound():
+    """On a line the monotone coupling is optimal for a convex cost: p* (exact, O(n log n) on the
+    host) must lie in [L_best, U_best] at n = m = 2^17 with non-uniform weights, and the gap closes."""
+    ctx = P.Context(0)
+    n = 1 << 17
+    x = I.random_cloud(n, 1, seed=21)
+    y = I.random_cloud(n, 1, seed=22)
+    a = I.uniform_weights(n, 23)
+    b = I.uniform_weights(n, 24)
+    pstar = O.pstar_1d(x[:, 0], a, y[:, 0], b, 1.0)
+    gaps = []
+    for iters in (100, 400):
+        f, g, res = ctx.solve(x, y, a, b, cost_scale=1.0, omega=1.0, eps0=1.0, lam=1.0, max_iters=iters,
+                              cert_every=50)
+        assert res["L_best"] <= pstar + 1e-12 and pstar <= res["U_best"] + 1e-12, (iters, res, pstar)
+        gaps.append(res["U_best"] - res["L_best"])
+    assert gaps[1] < gaps[0]
+    ctx.close()
