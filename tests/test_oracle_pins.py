@@ -334,3 +334,47 @@ def test_planted_mistake_wrong_eps_in_certificate_breaks_normalisation():
     bad = O.certificate(st.log_alpha_hat, st.log_beta_hat, st.log_beta_tilde, r, c, C,
                         O.eps_schedule(1.0, 1.0, st.k - 2), 1.0)  # eta_{k-1} instead of eta_k
     assert np.abs(st.log_beta_hat - (np.log(c) - bad["d"])).max() > 1e-3
+
+
+# ---- barycentric projection and marginal errors (App. G output; Tables 3 and 4) ----
+
+def test_projection_closed_form_when_cost_depends_on_column_only():
+    """All sources at the origin: C_ij = kappa ||y_j||^2 for every i, so each row of X is proportional
+    to w_j = v_j exp(-kappa ||y_j||^2 / eps) and every source is sent to the same w-weighted mean of
+    y; the row sums are u_i sum_j w_j and the column sums w_j sum_i u_i."""
+    rng = np.random.default_rng(3)
+    n, m, kappa, eps = 6, 9, 0.7, 0.3
+    x = np.zeros((n, 2))
+    y = rng.random((m, 2))
+    log_u = rng.normal(size=n)
+    log_v = rng.normal(size=m)
+    C = O.cost_matrix(x, y, kappa)
+    d = O.plan_diagnostics(log_u, log_v, C, eps, y, np.full(n, 1 / n), np.full(m, 1 / m))
+    w = np.exp(log_v - kappa * (y ** 2).sum(1) / eps)
+    mean = (w[:, None] * y).sum(0) / w.sum()
+    assert np.allclose(d["y_hat"], mean[None, :], rtol=0, atol=1e-13)
+    assert np.allclose(d["row_sums"], np.exp(log_u) * w.sum(), rtol=1e-13)
+    assert np.allclose(d["col_sums"], w * np.exp(log_u).sum(), rtol=1e-13)
+
+
+def test_plan_marginals_of_the_iterates():
+    """From Algorithm 1's iterates: diag(A) K diag(B) with B = c / (K^T A) has column sums c, and the
+    intermediate plan diag(alpha-hat) K diag(beta-tilde) has row sums r (Prop. 3; App. F); both carry
+    the same total mass on either side and project inside the convex hull of the targets."""
+    prob = I.grid_problem(6, 5, "gaussmix", "cauchy")
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    a, b = prob.a, prob.b
+    st = O.dual_obdrs(a, b, C, 1.0, 1.5, 40)
+    Y = O.plan_diagnostics(st.log_alpha_hat, st.log_beta_hat, C, st.eps, prob.y, a, b)
+    Z = O.plan_diagnostics(st.log_alpha_hat, st.log_beta_tilde, C, st.eps, prob.y, a, b)
+    assert Y["col_max_rel"] < 1e-12 and Y["row_l1"] > 1e-8
+    assert Z["row_max_rel"] < 1e-12
+    for D in (Y, Z):
+        assert abs(D["row_sums"].sum() - D["col_sums"].sum()) < 1e-13
+        assert (D["y_hat"] >= prob.y.min(0) - 1e-12).all() and (D["y_hat"] <= prob.y.max(0) + 1e-12).all()
+    # the sampled, on-the-fly form agrees with the dense one
+    rows = np.array([0, 7, 35])
+    lr, yh = O.projection_sampled(rows, prob.x, prob.y, st.log_alpha_hat, st.log_beta_hat, prob.kappa, st.eps,
+                                  chunk=5)
+    assert np.allclose(np.exp(lr), Y["row_sums"][rows], rtol=1e-12)
+    assert np.allclose(yh, Y["y_hat"][rows], rtol=0, atol=1e-12)
