@@ -177,6 +177,34 @@ ot_status ot_state_set(ot_state* st, int which, const double* in, int64_t k);
 ot_status ot_state_cost(ot_state* st, double* kappa, double* omega);
 
 /* ---------------------------------------------------------------------------------------------
+ * Output of the colour-transfer application (App. G, "Implicit implementation and output"; the
+ * marginal errors of Tables 3 and 4).  For an implicit plan X = diag(u) K diag(v), K = exp(-C/eps),
+ * never formed, ot_plan_project computes
+ *   - the barycentric projection y_hat[i] = sum_j X_ij y_j / sum_j X_ij (n x d floats, row-major),
+ *   - the row sums (n doubles) and column sums (m doubles) of X,
+ *   - their errors against r and c: l1, maximum absolute, maximum relative to the prescribed mass.
+ * The plan is chosen by `plan`:
+ *   OT_PLAN_BEST          u = exp(f/eps), v = c exp(g/eps) from the certificate potentials f, g of
+ *                         the best certificate iteration (the iterate the paper keeps); its column
+ *                         sums equal c.  Needs at least one certificate, else OT_EINVAL.
+ *   OT_PLAN_LATEST        u = alpha-hat, v = beta-hat of the last completed iteration.
+ *   OT_PLAN_INTERMEDIATE  u = alpha-hat, v = beta-tilde of the last completed iteration: the
+ *                         intermediate plan of Prop. 3, whose row sums equal r.
+ * eps is that iteration's temperature (returned in err->eps).  Exponents are formed in
+ * float-float and sums are Kahan-compensated FP32 (relative error of the sums ~1e-7).  Outputs are
+ * host pointers, each may be NULL.  The call allocates temporary device memory (about
+ * 24 (n + m) bytes plus repacked operands), waits for the state's stream, and returns OT_ENOMEM if
+ * that allocation fails. */
+typedef enum { OT_PLAN_BEST = 0, OT_PLAN_LATEST = 1, OT_PLAN_INTERMEDIATE = 2 } ot_plan_kind;
+typedef struct {
+  double row_l1, row_max_abs, row_max_rel; /* row sums against r */
+  double col_l1, col_max_abs, col_max_rel; /* column sums against c */
+  double eps;                              /* temperature of the plan */
+} ot_marginal_errors;
+ot_status ot_plan_project(ot_state* st, int32_t plan, float* y_hat, double* row_sums, double* col_sums,
+                          ot_marginal_errors* err);
+
+/* ---------------------------------------------------------------------------------------------
  * Continuous-batching server.  Not in the paper: a serving front end for many independent solves
  * on one GPU.  ot_serve_submit copies the problem (host arrays, or device arrays when
  * on_device = 1) and queues it; a scheduler thread admits queued requests in arrival order into

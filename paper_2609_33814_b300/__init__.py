@@ -92,6 +92,15 @@ _lib.ot_certificate.argtypes = [_P, C.POINTER(OtResult)]
 _lib.ot_state_get.argtypes = [_P, C.c_int, _P, C.POINTER(C.c_int64)]
 _lib.ot_state_set.argtypes = [_P, C.c_int, _P, C.c_int64]
 _lib.ot_state_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+
+
+class OtMarginalErrors(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("row_l1", "row_max_abs", "row_max_rel", "col_l1", "col_max_abs",
+                                          "col_max_rel", "eps")]
+
+
+OT_PLAN_BEST, OT_PLAN_LATEST, OT_PLAN_INTERMEDIATE = range(3)
+_lib.ot_plan_project.argtypes = [_P, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(OtMarginalErrors)]
 _lib.ot_serve_create.argtypes = [_P, C.c_size_t, C.c_int32, C.c_uint64, C.POINTER(_P)]
 _lib.ot_serve_submit.argtypes = [_P, C.POINTER(OtProblem), C.POINTER(OtParams), C.POINTER(C.c_uint64)]
 _lib.ot_serve_poll.argtypes = [_P, C.c_uint64, _P, _P, C.POINTER(OtResult)]
@@ -239,7 +248,7 @@ class State:
         h = _P()
         ctx.check(_lib.ot_state_create(ctx.handle, C.byref(prob), C.byref(prm), C.byref(h)), "ot_state_create")
         self._h = h
-        self.n, self.m = int(prob.n), int(prob.m)
+        self.n, self.m, self.d = int(prob.n), int(prob.m), int(prob.d)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -278,6 +287,16 @@ class State:
     def set(self, which: int, values, k: int):
         v = _host(values, np.float64)
         self.ctx.check(_lib.ot_state_set(self._h, int(which), v.ctypes.data, int(k)), "ot_state_set")
+
+    def project(self, plan: int = OT_PLAN_BEST):
+        """``ot_plan_project``: (y_hat [n, d] float32, row sums [n], column sums [m], errors dict)."""
+        y_hat = np.empty((self.n, self.d), np.float32)
+        row = np.empty(self.n, np.float64)
+        col = np.empty(self.m, np.float64)
+        err = OtMarginalErrors()
+        self.ctx.check(_lib.ot_plan_project(self._h, int(plan), y_hat.ctypes.data, row.ctypes.data, col.ctypes.data,
+                                            C.byref(err)), "ot_plan_project")
+        return y_hat, row, col, {k: getattr(err, k) for k, _ in OtMarginalErrors._fields_}
 
     def cost(self):
         kap, om = C.c_double(), C.c_double()

@@ -18,6 +18,9 @@
 namespace ot {
 
 size_t sweep_smem_bytes();
+size_t plan_scratch_bytes(int64_t n, int64_t m);
+cudaError_t plan_diagnostics(const Inst& h, int which, double eps, const double* f_best, const double* g_best,
+                             void* scratch, float* y_hat, double* row, double* col, double* err, cudaStream_t st);
 cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int iters, int grid,
                          unsigned* sched, cudaStream_t stream);
 cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
@@ -882,6 +885,69 @@ ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* 
   if (entries) *entries = s.entries;
   if (ms) *ms = s.ms;
   return OT_OK;
+}
+
+ot_status ot_plan_project(ot_state* st, int32_t plan, float* y_hat, double* row_sums, double* col_sums,
+                          ot_marginal_errors* err) {
+  if (!st || plan < OT_PLAN_BEST || plan > OT_PLAN_INTERMEDIATE) return OT_EINVAL;
+  Context& ctx = st->ctx->c;
+  Instance& in = st->in;
+  cudaSetDevice(ctx.device);
+  double eps;
+  if (plan == OT_PLAN_BEST) {
+    if (in.best_iter < 0) {
+      ctx.set_error("no certificate has been computed yet");
+      return OT_EINVAL;
+    }
+    eps = in.h.eta / (in.h.lambda * (double)in.best_iter + 1.0);
+  } else {
+    if (in.k < 1) {
+      ctx.set_error("the state has no completed iteration");
+      return OT_EINVAL;
+    }
+    eps = in.h.eta / (in.h.lambda * (double)(in.k - 1) + 1.0);
+  }
+  const int64_t n = in.n, m = in.m;
+  // one temporary allocation: working memory, then the device outputs
+  const size_t o_y = (plan_scratch_bytes(n, m) + 255) & ~(size_t)255;
+  const size_t o_row = (o_y + sizeof(float) * n * in.d + 255) & ~(size_t)255;
+  const size_t o_col = (o_row + sizeof(double) * n + 255) & ~(size_t)255;
+  const size_t o_err = (o_col + sizeof(double) * m + 255) & ~(size_t)255;
+  const size_t bytes = o_err + 6 * sizeof(double);
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx.set_error("device allocation of %zu bytes failed", bytes);
+    return OT_ENOMEM;
+  }
+  ot_status status = OT_OK;
+  double herr[6] = {0, 0, 0, 0, 0, 0};
+  cudaError_t e = plan_diagnostics(in.h, plan, eps, in.f_best, in.g_best, mem, (float*)(mem + o_y),
+                                   (double*)(mem + o_row), (double*)(mem + o_col), (double*)(mem + o_err), in.stream);
+  ctx.launches += 7;
+  if (e == cudaSuccess && y_hat)
+    e = cudaMemcpyAsync(y_hat, mem + o_y, sizeof(float) * n * in.d, cudaMemcpyDeviceToHost, in.stream);
+  if (e == cudaSuccess && row_sums)
+    e = cudaMemcpyAsync(row_sums, mem + o_row, sizeof(double) * n, cudaMemcpyDeviceToHost, in.stream);
+  if (e == cudaSuccess && col_sums)
+    e = cudaMemcpyAsync(col_sums, mem + o_col, sizeof(double) * m, cudaMemcpyDeviceToHost, in.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(herr, mem + o_err, sizeof(herr), cudaMemcpyDeviceToHost, in.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(in.stream);
+  if (e != cudaSuccess) {
+    ctx.set_error("plan diagnostics failed: %s", cudaGetErrorString(e));
+    status = OT_ECUDA;
+  }
+  cudaFree(mem);
+  if (status == OT_OK && err) {
+    err->row_l1 = herr[0];
+    err->row_max_abs = herr[1];
+    err->row_max_rel = herr[2];
+    err->col_l1 = herr[3];
+    err->col_max_abs = herr[4];
+    err->col_max_rel = herr[5];
+    err->eps = eps;
+  }
+  return status;
 }
 
 ot_status ot_state_cost(ot_state* st, double* kappa, double* omega) {
