@@ -22,10 +22,11 @@ constexpr int kPlanR = 2;                      // points per thread
 constexpr int kPlanCh = 8;                     // columns per chunk (one maximum and rescale test)
 constexpr int kPlanChunkPts = 2048;            // points per block of the error reduction
 constexpr double kL2e = 1.4426950408889634074;
-// The shift follows the running maximum exactly (rescale whenever a chunk exceeds it): the
-// exponent is rounded to FP32 relative to the shift, so the dominant terms must sit near 0, where
-// that rounding costs < 2^-24 in log2 (a lazy threshold of 32 would cost up to 32 * 2^-24).
-constexpr float kPlanTau = 0.0f;
+// The exponent is exact in float-float until it is rounded to FP32 relative to the shift, so the
+// shift follows the maximum closely (rescale when a chunk exceeds it by more than 1: the dominant
+// terms stay within 2 of it, where that rounding costs < 2^-23 in log2), and a chunk whose shift
+// moves is evaluated again against the new shift.
+constexpr float kPlanTau = 1.0f;
 
 __device__ __forceinline__ size_t pk_idx(int p, int comp) {
   return ((size_t)(p / kTQ) * kNComp + comp) * kTQ + (p % kTQ);
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
     __syncthreads();
     for (int c0 = 0; c0 < kTQ; c0 += kPlanCh) {
       float v[kPlanR][kPlanCh];
+      auto eval = [&]() {
 #pragma unroll
       for (int cc = 0; cc < kPlanCh; ++cc) {
         const int c = c0 + cc;
@@ -115,6 +117,9 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
           v[r][cc] = __fadd_rn(sb, lo);
         }
       }
+      };
+      eval();
+      bool moved = false;
 #pragma unroll
       for (int r = 0; r < kPlanR; ++r) {
         float cm = v[r][0];
@@ -133,10 +138,10 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
             }
           }
           mref[r] += sh;
-#pragma unroll
-          for (int cc = 0; cc < kPlanCh; ++cc) v[r][cc] -= sh;
+          moved = true;
         }
       }
+      if (moved) eval();  // against the new shifts
       fresh = false;
 #pragma unroll
       for (int r = 0; r < kPlanR; ++r) {

@@ -526,9 +526,16 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       } else {
         // compensated (float-float) or FP64 exponent
         typedef typename std::conditional<MODE == kSweepF64, double, float>::type V;
+        // The compensated exponent is exact only until it is rounded to FP32 relative to the
+        // shift, so its shift follows the maximum closely (threshold 1: the dominant terms stay
+        // within 2 of it) and a chunk whose shift moves is evaluated again against the new shift;
+        // subtracting the new shift from values rounded against the old one would keep their
+        // rounding, up to |old shift - value| * 2^-24.  FP64 loses nothing by subtracting.
+        constexpr V tau = MODE == kSweepF64 ? (V)kTau : (V)1;
 #pragma unroll 1
         for (int c0 = 0; c0 < kTQ; c0 += CH) {
           V v[R][CH];
+          auto eval = [&]() {
 #pragma unroll
           for (int cc = 0; cc < CH; ++cc) {
             const int c = c0 + cc;
@@ -560,6 +567,8 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
               }
             }
           }
+          };
+          eval();
           V cm[R];
           bool need = fresh;
 #pragma unroll
@@ -568,12 +577,12 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
 #pragma unroll
             for (int cc = 1; cc < CH; ++cc) mx = mx > v[r][cc] ? mx : v[r][cc];
             cm[r] = mx;
-            need |= mx > (V)kTau;
+            need |= mx > tau;
           }
           if (__any_sync(0xffffffffu, need)) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-              if (fresh || cm[r] > (V)kTau) {
+              if (fresh || cm[r] > tau) {
                 const V sh = floor(cm[r]);
                 if (!fresh) {
                   if constexpr (MODE == kSweepF64) {
@@ -588,10 +597,13 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
                   }
                 }
                 st.mref[r] += sh;
+                if constexpr (MODE == kSweepF64) {
 #pragma unroll
-                for (int cc = 0; cc < CH; ++cc) v[r][cc] -= sh;
+                  for (int cc = 0; cc < CH; ++cc) v[r][cc] -= sh;
+                }
               }
             }
+            if constexpr (MODE != kSweepF64) eval();
           }
           fresh = false;
           V cs[R], cn[R];
