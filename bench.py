@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--tol-rel", type=float, default=0.01)
     ap.add_argument("--seed", type=int, default=2609)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--workload", default="serve", choices=["serve", "sweep"],
+    ap.add_argument("--workload", default="serve", choices=["serve", "sweep", "project"],
                     help="serve: the serving stream (the bench line); sweep: one resident instance, "
                          "fast iterations only (kernel roofline and profiling)")
     ap.add_argument("--size", type=int, default=512, help="sweep workload: s for an s x s grid, or -n for "
@@ -446,6 +446,49 @@ def run_ours(args, rank: int, world: int):
         td.barrier()
 
 
+def run_project(args):
+    """Barycentric projection and marginal errors (ot_plan_project) of one solved instance: implicit
+    entries/s over the row pass (with the d projection sums) and the column pass, 2 n m per call."""
+    import torch
+    import paper_2609_33814_b300 as P
+    prob = I.grid_problem(args.size, args.seed) if args.size > 0 else I.rgb_problem(-args.size, args.seed)
+    ctx = P.Context(0)
+    dev = [torch.from_numpy(v).cuda() for v in (prob.x, prob.y, prob.a, prob.b)]
+    S = ctx.state(*dev, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0 if args.size > 0 else 0.1,
+                  precision="mufu", cert_every=args.iters)
+    S.step(args.iters)  # one certificate iteration: the plan of the best certificate exists
+    for _ in range(args.warmup):
+        S.project(P.OT_PLAN_BEST)
+    clock = ClockSampler(0)
+    clock.start()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, _, _, err = S.project(P.OT_PLAN_BEST)
+        times.append(time.perf_counter() - t)
+    clocks = clock.stop()
+    t_call = statistics.median(times)
+    entries = 2.0 * prob.n * prob.m
+    d = prob.d
+    # FP32 lane operations per entry (float-float exponent 8 + 11 d, maximum, sum; d projection FMAs on
+    # the row pass), averaged over the two passes
+    ops = ((9 + 12 * d) + (9 + 11 * d)) / 2.0
+    peak = 128.0 / ops * 148 * (clocks.get("sm_max_mhz") or 2032.0) * 1e6
+    out = {"metric": "implicit entries/s, barycentric projection and marginal errors", "value": entries / t_call,
+           "unit": "entries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_call, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 float-float exponent, f32 Kahan sums", "data": "synthetic",
+           "config": {"workload": f"{'grid %dx%d' % (args.size, args.size) if args.size > 0 else 'rgb %d' % -args.size}"
+                                  f" d={d}, plan of the best certificate", "n": prob.n, "m": prob.m,
+                      "timing": "wall time of ot_plan_project (its temporary allocation and result copies included)"},
+           "roofline": {"bound": "alu", "achieved": entries / t_call, "peak": peak, "unit": "entries/s",
+                        "frac": entries / t_call / peak, "traffic": None,
+                        "peak_basis": f"128 FP32 lanes / {ops:.1f} ops per entry per clk per SM x 148 SMs x sm_max_mhz"},
+           "marginal_errors": err, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(args):
     """One resident instance, fast iterations only: entries/s of the sweep kernels alone."""
     import ctypes
@@ -496,6 +539,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.workload == "sweep":
         run_sweep(args)
+        return
+    if args.workload == "project":
+        run_project(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
