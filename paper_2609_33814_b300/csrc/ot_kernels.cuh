@@ -8,7 +8,7 @@ namespace ot {
 constexpr int kThreads = 128;  // threads per CTA in every sweep kernel
 constexpr int kTQ = 128;       // points per shared-memory tile (per pipeline stage)
 constexpr int kStages = 4;     // TMA pipeline depth
-constexpr int kStageTiles = 2; // pack tiles per pipeline stage (one bulk copy, one CTA barrier)
+constexpr int kStageTiles = 4; // pack tiles per pipeline stage (one bulk copy, one CTA barrier)
 constexpr int kNComp = 5;      // pack components per point: up to 3 coords, h (hi), h (lo)
 constexpr uint32_t kWaitLimit = 1u << 26;  // mbarrier polls before a sweep gives up (~seconds)
 

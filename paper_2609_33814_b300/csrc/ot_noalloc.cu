@@ -94,7 +94,7 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
   splits = splits < 1 ? 1 : (splits > kMaxSplits ? kMaxSplits : splits);
   if (splits > tiles_y) splits = tiles_y;
   int tps = (tiles_y + splits - 1) / splits;
-  if (splits > 1 && (tps & 1)) ++tps;  // runs of an even number of tiles (pipeline stages of two)
+  if (splits > 1 && (tps & 1)) ++tps;  // runs of an even number of tiles, as the instance plans use
   splits = (tiles_y + tps - 1) / tps;
 
   Inst h{};

@@ -88,7 +88,8 @@ void canonical_tile(int d, int mode, int* R, int* ch) {
 
 // Micro-splits of one sweep of an instance: enough runs of the reduced side that any launch can
 // cut the instance into balanced work items (about 65536 point-block runs), each run at least 4
-// tiles and an even number of tiles (a pipeline stage never straddles two runs), at most 64 runs.
+// tiles and an even number of tiles, at most 64 runs (a run may end inside a pipeline stage: the
+// sweep closes runs tile by tile).
 // The layout depends only on the instance's sizes and the plan's R, so the instance's partials,
 // and hence its results, are the same in every launch that contains it.
 void micro_splits(int64_t np, int64_t nq, int R, int* nms, int* mst) {
