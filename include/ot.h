@@ -173,6 +173,19 @@ ot_status ot_state_get(ot_state* st, int which, double* out, int64_t* k);
  * the column operands of iteration k are rebuilt from them. */
 ot_status ot_state_set(ot_state* st, int which, const double* in, int64_t k);
 
+/* Tile plans (not part of the method: a tuning table).  Every instance uses the plan of its (d,
+ * precision): points per thread R and chunk width CH of its sweep kernel.  The plans come from the
+ * built-in table (the autotuner's choices on B300), then from tile_plans.txt beside the library
+ * (written by paper_2609_33814_b300/autotune.py, read when the first context is created; the
+ * environment variable OT_TILE_PLANS names another file), then from ot_set_tile_plan.  A plan applies
+ * to states and server lanes created afterwards; it changes results bitwise (summation order), never
+ * their accuracy.  R = 0 restores the built-in plan; OT_EINVAL for a (d, precision, R, CH) whose
+ * kernel is not built (fast modes: R in {1, 2, 4} with CH in {8, 16} or R = 8 with CH = 8, the
+ * polynomial modes R in {2, 4} with CH = 16; compensated: R in {1, 2, 4}, CH = 8; FP64: R in {1, 2},
+ * CH = 8). */
+ot_status ot_set_tile_plan(int32_t d, int32_t precision, int32_t R, int32_t ch);
+ot_status ot_get_tile_plan(int32_t d, int32_t precision, int32_t* R, int32_t* ch);
+
 /* The (kappa, omega) the state uses, after any device-side cost-range pass. */
 ot_status ot_state_cost(ot_state* st, double* kappa, double* omega);
 

@@ -92,6 +92,8 @@ _lib.ot_certificate.argtypes = [_P, C.POINTER(OtResult)]
 _lib.ot_state_get.argtypes = [_P, C.c_int, _P, C.POINTER(C.c_int64)]
 _lib.ot_state_set.argtypes = [_P, C.c_int, _P, C.c_int64]
 _lib.ot_state_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.ot_set_tile_plan.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+_lib.ot_get_tile_plan.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
 
 
 class OtMarginalErrors(C.Structure):
@@ -390,3 +392,21 @@ def probe_exp2(x, method: str = "poly", device: int = 0) -> np.ndarray:
     if st != OT_OK:
         raise OTError(st, "ot_probe_exp2")
     return out
+
+
+
+
+def set_tile_plan(d: int, precision: str, R: int, ch: int) -> None:
+    """``ot_set_tile_plan``: the (R, CH) of the sweep kernels of (d, precision); R = 0 resets."""
+    st = _lib.ot_set_tile_plan(int(d), PRECISIONS[precision], int(R), int(ch))
+    if st != OT_OK:
+        raise OTError(st, f"ot_set_tile_plan({d}, {precision}, {R}, {ch})")
+
+
+def get_tile_plan(d: int, precision: str):
+    """``ot_get_tile_plan``: the (R, CH) instances of (d, precision) use now."""
+    R, ch = C.c_int32(), C.c_int32()
+    st = _lib.ot_get_tile_plan(int(d), PRECISIONS[precision], C.byref(R), C.byref(ch))
+    if st != OT_OK:
+        raise OTError(st, "ot_get_tile_plan")
+    return int(R.value), int(ch.value)

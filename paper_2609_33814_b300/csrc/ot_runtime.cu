@@ -8,8 +8,11 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
+
+#include <dlfcn.h>
 
 #include "../../include/ot.h"
 #include "ot_kernels.cuh"
@@ -70,7 +73,19 @@ static int env_int(const char* name, int dflt) {
 // (d, precision mode), the split counts only on the instance's own sizes.  An instance therefore
 // produces bitwise the same results alone or inside any batch; only the launch grid (which does
 // not affect results) depends on the device's occupancy.
-void canonical_tile(int d, int mode, int* R, int* ch) {
+//
+// The plan per (d, mode) comes from a table that the autotuner (autotune.py beside this library)
+// fills by timing every instantiated (R, CH) on the device and writes to tile_plans.txt; the table
+// is loaded when the first context is created (OT_TILE_PLANS names another file, empty: none) and
+// can be set with ot_set_tile_plan.  Entries left unset use the built-in plans below, which are the
+// autotuner's choices on B300.  A table changes results bitwise (another summation order), never
+// their accuracy.
+namespace {
+std::mutex g_plan_mu;
+int g_plan[4][5][2] = {};  // [d][mode] -> {R, CH}; R = 0: built-in
+}  // namespace
+
+static void builtin_tile(int d, int mode, int* R, int* ch) {
   if (mode == kSweepF64) {
     *R = 1;
     *ch = 8;
@@ -84,6 +99,56 @@ void canonical_tile(int d, int mode, int* R, int* ch) {
     *R = 2;
     *ch = 16;
   }
+}
+
+void canonical_tile(int d, int mode, int* R, int* ch) {
+  builtin_tile(d, mode, R, ch);
+  if (d < 1 || d > 3 || mode < 0 || mode > 4) return;
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (g_plan[d][mode][0] > 0) {
+    *R = g_plan[d][mode][0];
+    *ch = g_plan[d][mode][1];
+  }
+}
+
+// Sets the table entry of (d, mode); R = 0 restores the built-in plan.  False if that kernel is not
+// instantiated.
+static bool set_tile(int d, int mode, int R, int ch) {
+  if (d < 1 || d > 3 || mode < 0 || mode > 4) return false;
+  if (R != 0 && !get_sweep(d, mode, R, ch, 0)) return false;
+  if (R != 0 && (mode == kSweepComp || mode == kSweepF64) && ch != 8) return false;  // built with CH = 8 only
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_plan[d][mode][0] = R;
+  g_plan[d][mode][1] = R ? ch : 0;
+  return true;
+}
+
+int sweep_mode_of(int precision);
+
+// Lines "d precision R CH" (ot_precision values; '#' starts a comment); invalid lines are skipped.
+static void load_tile_plans() {
+  std::string path;
+  if (const char* e = getenv("OT_TILE_PLANS")) {
+    path = e;
+  } else {
+    Dl_info info;
+    if (dladdr((void*)&load_tile_plans, &info) && info.dli_fname) {
+      path = info.dli_fname;
+      const size_t slash = path.rfind('/');
+      path = (slash == std::string::npos ? std::string(".") : path.substr(0, slash)) + "/tile_plans.txt";
+    }
+  }
+  if (path.empty()) return;
+  FILE* f = fopen(path.c_str(), "r");
+  if (!f) return;
+  char line[256];
+  while (fgets(line, sizeof(line), f)) {
+    if (char* h = strchr(line, '#')) *h = 0;
+    int d, prec, R, ch;
+    if (sscanf(line, "%d %d %d %d", &d, &prec, &R, &ch) == 4 && prec >= 0 && prec <= 4)
+      set_tile(d, sweep_mode_of(prec), R, ch);
+  }
+  fclose(f);
 }
 
 // Micro-splits of one sweep of an instance: enough runs of the reduced side that any launch can
@@ -712,6 +777,8 @@ ot_status ot_context_create(int device, ot_context** out) {
     return OT_EINVAL;
   }
   if (cudaSetDevice(device) != cudaSuccess) return OT_ECUDA;
+  static std::once_flag plans_once;
+  std::call_once(plans_once, load_tile_plans);
   ot_context* c = new (std::nothrow) ot_context();
   if (!c) return OT_ENOMEM;
   c->c.device = device;
@@ -949,6 +1016,20 @@ ot_status ot_plan_project(ot_state* st, int32_t plan, float* y_hat, double* row_
     err->eps = eps;
   }
   return status;
+}
+
+ot_status ot_set_tile_plan(int32_t d, int32_t precision, int32_t R, int32_t ch) {
+  if (precision < OT_EXP_MUFU || precision > OT_FP32_COMP) return OT_EINVAL;
+  return set_tile(d, sweep_mode_of(precision), R, ch) ? OT_OK : OT_EINVAL;
+}
+
+ot_status ot_get_tile_plan(int32_t d, int32_t precision, int32_t* R, int32_t* ch) {
+  if (d < 1 || d > 3 || precision < OT_EXP_MUFU || precision > OT_FP32_COMP || !R || !ch) return OT_EINVAL;
+  int r, c;
+  canonical_tile(d, sweep_mode_of(precision), &r, &c);
+  *R = r;
+  *ch = c;
+  return OT_OK;
 }
 
 ot_status ot_state_cost(ot_state* st, double* kappa, double* omega) {

@@ -104,11 +104,17 @@ struct Server {
 
 static const int kMaxLaunch = 2;  // fast iterations, certificate iteration
 
+// A lane runs instances of one (d, mode, cert_every) and one tile plan (the plans are taken from the
+// prepared instance, so a plan table changed between submissions opens a new lane).
 int Server::lane_for(const Request* r) {
   const int mode = sweep_mode_of(r->params.precision);
+  const LaunchPlan& pf = r->inst->fast;
+  const LaunchPlan& pc = r->inst->cert;
   for (int i = 0; i < nlanes; ++i) {
     const Lane& L = lanes[i];
-    if (L.d == r->prob.d && L.mode == mode && L.ce == r->params.cert_every) return i;
+    if (L.d == r->prob.d && L.mode == mode && L.ce == r->params.cert_every && L.R_fast == pf.R &&
+        L.ch_fast == pf.ch && L.R_cert == pc.R)
+      return i;
   }
   if (nlanes == kMaxLanes) return -1;
   Lane& L = lanes[nlanes];
@@ -116,9 +122,9 @@ int Server::lane_for(const Request* r) {
   L.mode = mode;
   L.cert_mode = mode == kSweepF64 ? kSweepF64 : kSweepComp;
   L.ce = r->params.cert_every;
-  int ch_cert = 8;
-  canonical_tile(L.d, L.mode, &L.R_fast, &L.ch_fast);
-  canonical_tile(L.d, L.cert_mode, &L.R_cert, &ch_cert);
+  L.R_fast = pf.R;
+  L.ch_fast = pf.ch;
+  L.R_cert = pc.R;
   return nlanes++;
 }
 
@@ -571,9 +577,11 @@ ot_status ot_serve_submit(ot_server* sv, const ot_problem* prob, const ot_params
   r->inst = new Instance();
   r->inst->async_alloc = true;
   r->inst->use_graphs = false;
-  r->lane = S.lane_for(r);
-  ot_status st = r->lane < 0 ? OT_EINVAL : OT_OK;
-  if (st == OT_OK) st = instance_prepare(S.ctx, *r->inst, &r->prob, &r->params, S.ctx.stream);
+  ot_status st = instance_prepare(S.ctx, *r->inst, &r->prob, &r->params, S.ctx.stream);
+  if (st == OT_OK) {
+    r->lane = S.lane_for(r);  // a lane of the instance's own tile plans
+    if (r->lane < 0) st = OT_EINVAL;
+  }
   r->bytes = r->inst->bytes;
   if (st == OT_OK && r->bytes > S.budget) st = OT_ENOMEM;
   if (st != OT_OK) {

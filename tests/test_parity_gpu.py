@@ -241,3 +241,38 @@ def test_full_size_rgb_sampled_rows(ctx):
     err = np.abs(eta * (lah[rows] - ref)).max() / np.abs(eta * ref).max()
     assert err <= 1e-5, err
     S.close()
+
+
+def test_non_default_tile_plan_parity_and_server_lanes(ctx):
+    """A state created under another tile plan still matches the oracle one step at a time, and a
+    server keeps requests of different plans in different lanes (both correct)."""
+    prob = _problem("grid32", 5)
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    a = prob.a / prob.a.sum()
+    b = prob.b / prob.b.sum()
+    try:
+        P.set_tile_plan(2, "mufu", 4, 8)
+        S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0,
+                      precision="mufu", cert_every=0)
+        S.step(3)
+        st = O.DualState(S.get(P.OT_LOG_ALPHA), S.get(P.OT_LOG_BETA), S.get(P.OT_LOG_BETA_PREV),
+                         S.get(P.OT_LOG_ALPHA_HAT), S.get(P.OT_LOG_BETA_HAT), S.get(P.OT_LOG_BETA_TILDE), 3,
+                         O.eps_schedule(1.0, 1.0, 2))
+        st1 = O.dual_obdrs_step(st, np.log(a), np.log(b), C, 1.0, 1.0)
+        S.step(1)
+        err = _potential_err(st1, S.get(P.OT_LOG_ALPHA_HAT), S.get(P.OT_LOG_BETA_HAT), st1.eps, np.log(b))
+        assert err <= TOL_POT["mufu"], err
+        S.close()
+        srv = P.Server(ctx, hbm_budget_bytes=1 << 30, max_slots=8)
+        r1 = srv.submit(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, max_iters=100,
+                        cert_every=50)
+        P.set_tile_plan(2, "mufu", 0, 0)
+        r2 = srv.submit(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, max_iters=100,
+                        cert_every=50)
+        f1, g1, res1 = srv.wait(r1, 60.0)
+        f2, g2, res2 = srv.wait(r2, 60.0)
+        scale = max(np.abs(f2).max(), np.abs(g2).max())
+        assert np.abs(f1 - f2).max() / scale <= 1e-4 and abs(res1["U_best"] - res2["U_best"]) <= 1e-6
+        srv.close()
+    finally:
+        P.set_tile_plan(2, "mufu", 0, 0)
