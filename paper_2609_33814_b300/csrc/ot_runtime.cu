@@ -85,20 +85,18 @@ std::mutex g_plan_mu;
 int g_plan[4][5][2] = {};  // [d][mode] -> {R, CH}; R = 0: built-in
 }  // namespace
 
+// Built-in plans: the autotuner's choices on B300 (tile_plans.txt in the package holds its
+// measurements), indexed [d - 1][mode] with modes fast, compensated, FP64, fast+poly, fast+split.
 static void builtin_tile(int d, int mode, int* R, int* ch) {
-  if (mode == kSweepF64) {
-    *R = 1;
-    *ch = 8;
-  } else if (mode == kSweepComp) {
-    *R = 2;
-    *ch = 8;
-  } else if (d == 3) {
-    *R = 4;
-    *ch = 16;
-  } else {
-    *R = 2;
-    *ch = 16;
-  }
+  static const int kPlan[3][5][2] = {
+      {{2, 16}, {2, 8}, {2, 8}, {2, 16}, {2, 16}},  // d = 1
+      {{2, 16}, {1, 8}, {1, 8}, {4, 16}, {2, 16}},  // d = 2
+      {{4, 8}, {1, 8}, {2, 8}, {2, 16}, {4, 16}},   // d = 3
+  };
+  const int di = (d >= 1 && d <= 3) ? d - 1 : 1;
+  const int mi = (mode >= 0 && mode <= 4) ? mode : 0;
+  *R = kPlan[di][mi][0];
+  *ch = kPlan[di][mi][1];
 }
 
 void canonical_tile(int d, int mode, int* R, int* ch) {
