@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--cert-every", type=int, default=100)
     ap.add_argument("--tol-rel", type=float, default=0.01)
+    ap.add_argument("--lam", type=float, default=1.5, help="arms workload: overrelaxation lambda")
     ap.add_argument("--seed", type=int, default=2609)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--workload", default="serve", choices=["serve", "sweep", "project"],
+    ap.add_argument("--workload", default="serve", choices=["serve", "sweep", "project", "arms"],
                     help="serve: the serving stream (the bench line); sweep: one resident instance, "
                          "fast iterations only (kernel roofline and profiling)")
     ap.add_argument("--size", type=int, default=512, help="sweep workload: s for an s x s grid, or -n for "
@@ -498,6 +499,68 @@ def run_project(args):
     print(json.dumps(out), flush=True)
 
 
+def run_arms(args):
+    """Batched O-BDRS arms at equal certified gap: 8 uneven instances (5 x 256^2, 3 x 512^2 grids,
+    classes cycling) in one server lane per arm, each run until its best certified relative gap is at
+    most --tol-rel.  Arms: MUFU exp2, the FMA-polynomial split and full polynomial, and FP64 (whose
+    time to gap is extrapolated from one measured iteration and the MUFU arm's iteration counts:
+    a full FP64 run at these sizes takes hours)."""
+    import torch
+    import paper_2609_33814_b300 as P
+    sizes = [256, 512, 256, 512, 256, 256, 512, 256]
+    classes = ["uniform", "gaussmix", "cauchy", "sparse"]
+    probs = [I.grid_problem(s, args.seed + i, classes[i % 4], classes[(i + 1) % 4]) for i, s in enumerate(sizes)]
+    dev = [[torch.from_numpy(v).cuda() for v in (p.x, p.y, p.a, p.b)] for p in probs]
+    ctx = P.Context(0)
+    lam = args.lam
+    arms = {}
+    clock = ClockSampler(0)
+    clock.start()
+    mufu_iters = None
+    for arm in ("mufu", "split", "poly"):
+        srv = P.Server(ctx, hbm_budget_bytes=64 << 30, max_slots=16)
+        srv.profile(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [srv.submit(*d, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15, eps0=1.0, lam=lam,
+                          max_iters=args.max_iters, cert_every=args.cert_every, tol_rel=args.tol_rel, precision=arm)
+               for d, p in zip(dev, probs)]
+        res = [srv.wait(r, 3600.0)[2] for r in ids]
+        wall = time.perf_counter() - t0
+        n, e, ms = srv.kernel_stats(0)
+        srv.close()
+        iters = [r["iters"] for r in res]
+        if arm == "mufu":
+            mufu_iters = iters
+        arms[arm] = {"fast_entries_per_s": e / ms * 1e3 if ms else None, "time_to_gap_s": wall,
+                     "iters": iters, "gap_rel": [r["gap_rel"] for r in res],
+                     "reached": all(r["stop"] == "tol" for r in res)}
+    # FP64: one iteration of a 256^2 instance for the rate
+    p0 = probs[0]
+    S = ctx.state(p0.x, p0.y, p0.a, p0.b, cost_scale=p0.kappa, omega=p0.omega, eps0=1.0, lam=lam, precision="fp64",
+                  cert_every=0)
+    S.step(1)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    S.step(1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    S.close()
+    fp64_rate = 2.0 * p0.n * p0.m / dt
+    work = sum(2.0 * p.n * p.m * k for p, k in zip(probs, mufu_iters))
+    arms["fp64"] = {"fast_entries_per_s": fp64_rate, "time_to_gap_s": work / fp64_rate, "extrapolated": True,
+                    "iters": mufu_iters}
+    clocks = clock.stop()
+    out = {"metric": "time to certified gap, batch of 8 uneven O-BDRS instances (MUFU arm)",
+           "value": arms["mufu"]["time_to_gap_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "per arm", "data": "synthetic",
+           "config": {"workload": "5 x 256^2 + 3 x 512^2 grid histograms, classes uniform/gaussmix/cauchy/sparse",
+                      "lambda": lam, "eps0": 1.0, "tol_rel": args.tol_rel, "cert_every": args.cert_every,
+                      "max_iters": args.max_iters},
+           "arms": arms, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(args):
     """One resident instance, fast iterations only: entries/s of the sweep kernels alone."""
     import ctypes
@@ -551,6 +614,9 @@ def main():
         return
     if args.workload == "project":
         run_project(args)
+        return
+    if args.workload == "arms":
+        run_arms(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
