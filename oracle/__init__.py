@@ -12,6 +12,9 @@ against the paper by eye:
 * ``cost_matrix``            - C_ij = kappa ||x_i - y_j||^2 (Sec. 2; App. G cost construction)
 * ``lse``                    - LSE as defined beside Algorithm 1, two-pass max-shifted
 * ``dual_obdrs_step``        - one iteration of Algorithm 1 (Dual O-BDRS, log domain)
+* ``ablation_step``          - the annealed-Sinkhorn ablation methods (AS, AS with momentum,
+                               current-kernel AS, DAS; App. B, App. G), log domain, and
+  ``ablation_primal``          their multiplicative forms with Hadamard powers of K
 * ``certificate``            - Proposition 3 with the stabilised upper bound of Algorithm 2
 * ``repair``                 - the feasible repair Z-hat from the proof of Proposition 3
 * ``primal_obdrs``           - primal (O-)BDRS, Eq. (bdrs) and Eq. (o_bdrs_x), dense non-log
@@ -126,6 +129,62 @@ def dual_obdrs_step(st: DualState, log_r: np.ndarray, log_c: np.ndarray, C: np.n
     return DualState(log_alpha=log_a, log_beta=log_b, log_beta_prev=st.log_beta,
                      log_alpha_hat=log_ah, log_beta_hat=log_bh, log_beta_tilde=log_bt,
                      k=k + 1, eps=eps)
+
+
+# Annealed-Sinkhorn ablation (App. B "Annealed Sinkhorn Detailed Comparison", App. G "Momentum and
+# Kernel Ablation"): methods that differ from Dual BDRS only in the row update, under the same
+# inverse-linear schedule (lam = 1):
+#   kernel   "old": K^(k) = exp(-C / eta_{k-1}) (eta_{-1} = infinity: K^(0) = 1), "current": K^(k+1)
+#   scaling  no momentum: v^{k-1};  momentum: (v^{k-1})^2 / v^{k-2}
+#   DAS      old kernel, no momentum, numerator (u^{k-1})^theta_k r with theta_1 = 0, theta_k = 1/k
+ALGORITHMS = {
+    "bdrs": ("current", True, False),
+    "as": ("old", False, False),
+    "as_momentum": ("old", True, False),
+    "as_current": ("current", False, False),
+    "das": ("old", False, True),
+}
+
+
+def das_theta(k: int) -> float:
+    """theta_k = 1 - eta_{k-1} / eta_{max(k-2, 0)} under eta_k = eta / (k + 1): 0 for k <= 1, 1/k after."""
+    return 0.0 if k <= 1 else 1.0 / k
+
+
+def ablation_step(st: DualState, log_r, log_c, C, eta: float, algorithm: str) -> DualState:
+    """One iteration k of an ablation method in the log domain (lam = 1, so alpha = alpha-hat)."""
+    kernel, momentum, debias = ALGORITHMS[algorithm]
+    k = st.k
+    eps = eps_schedule(eta, 1.0, k)                                  # column update: current kernel
+    inv_row = (k / eta) if kernel == "old" else (1.0 / eps)          # 1 / eta_{k-1} (0 at k = 0) or 1 / eta_k
+    log_bt = st.log_beta + (st.log_beta - st.log_beta_prev) if momentum else st.log_beta.copy()
+    log_ah = log_r - lse(log_bt[None, :] - C * inv_row, axis=1)
+    if debias:
+        log_ah = log_ah + das_theta(k) * st.log_alpha
+    log_bh = log_c - lse(log_ah[:, None] - C / eps, axis=0)
+    return DualState(log_alpha=log_ah, log_beta=log_bh, log_beta_prev=st.log_beta, log_alpha_hat=log_ah,
+                     log_beta_hat=log_bh, log_beta_tilde=log_bt, k=k + 1, eps=eps)
+
+
+def ablation_primal(r, c, C, eta: float, iters: int, algorithm: str):
+    """The same methods in the paper's multiplicative form with dense Hadamard powers of K = exp(-C/eta)
+    (small problems only): returns the lists of scalings u^k, v^k."""
+    kernel, momentum, debias = ALGORITHMS[algorithm]
+    K = np.exp(-np.asarray(C, np.float64) / eta)
+    u_prev = np.ones(len(r))
+    v1 = np.ones(len(c))   # v^{k-1}
+    v2 = np.ones(len(c))   # v^{k-2}
+    us, vs = [], []
+    for k in range(iters):
+        Krow = K ** k if kernel == "old" else K ** (k + 1)
+        vin = v1 * v1 / v2 if momentum else v1
+        num = r * (u_prev ** das_theta(k) if debias else 1.0)
+        u = num / (Krow @ vin)
+        v = c / ((K ** (k + 1)).T @ u)
+        us.append(u)
+        vs.append(v)
+        u_prev, v2, v1 = u, v1, v
+    return us, vs
 
 
 def dual_obdrs(r, c, C, eta, lam, iters, state: Optional[DualState] = None) -> DualState:

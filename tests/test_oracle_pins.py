@@ -378,3 +378,46 @@ def test_plan_marginals_of_the_iterates():
                                   chunk=5)
     assert np.allclose(np.exp(lr), Y["row_sums"][rows], rtol=1e-12)
     assert np.allclose(yh, Y["y_hat"][rows], rtol=0, atol=1e-12)
+
+
+# ---- annealed-Sinkhorn ablation methods (App. B; App. G "Momentum and Kernel Ablation") ----
+
+@pytest.mark.parametrize("alg", ["bdrs", "as", "as_momentum", "as_current", "das"])
+def test_ablation_log_domain_matches_multiplicative_form(alg):
+    """The log-domain row/column updates reproduce the paper's multiplicative updates with Hadamard
+    powers K^(k) / K^(k+1) of the base kernel (independent dense arithmetic) for every method."""
+    prob = I.grid_problem(4, 8, "gaussmix", "cauchy")
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    a, b = prob.a, prob.b
+    eta, iters = 1.0, 12
+    us, vs = O.ablation_primal(a, b, C, eta, iters, alg)
+    st = O.DualState.initial(len(a), len(b))
+    for k in range(iters):
+        st = O.ablation_step(st, np.log(a), np.log(b), C, eta, alg)
+        assert np.allclose(st.log_alpha_hat, np.log(us[k]), rtol=0, atol=1e-9), (alg, k)
+        assert np.allclose(st.log_beta_hat, np.log(vs[k]), rtol=0, atol=1e-9), (alg, k)
+
+
+def test_ablation_bdrs_corner_is_algorithm_1():
+    """The current-kernel, momentum corner of the 2x2 design is Dual BDRS itself (Algorithm 1 at lam = 1)."""
+    prob = I.grid_problem(5, 9, "uniform", "gaussmix")
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    s1 = O.DualState.initial(25, 25)
+    s2 = O.DualState.initial(25, 25)
+    for _ in range(15):
+        s1 = O.ablation_step(s1, np.log(prob.a), np.log(prob.b), C, 1.0, "bdrs")
+        s2 = O.dual_obdrs_step(s2, np.log(prob.a), np.log(prob.b), C, 1.0, 1.0)
+    assert np.allclose(s1.log_alpha_hat, s2.log_alpha_hat, rtol=0, atol=1e-12)
+    assert np.allclose(s1.log_beta_hat, s2.log_beta_hat, rtol=0, atol=1e-12)
+
+
+def test_ablation_planted_mistakes_break_the_pin():
+    """A wrong kernel power or a missing debiasing factor in the log-domain step fails the primal pin."""
+    prob = I.grid_problem(4, 8, "gaussmix", "cauchy")
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    us, _ = O.ablation_primal(prob.a, prob.b, C, 1.0, 6, "das")
+    us_as, _ = O.ablation_primal(prob.a, prob.b, C, 1.0, 6, "as")
+    us_cur, _ = O.ablation_primal(prob.a, prob.b, C, 1.0, 6, "as_current")
+    assert np.abs(np.log(us[5]) - np.log(us_as[5])).max() > 1e-3      # debiasing matters
+    assert np.abs(np.log(us_as[5]) - np.log(us_cur[5])).max() > 1e-3  # kernel timing matters
+    assert O.das_theta(0) == O.das_theta(1) == 0.0 and O.das_theta(4) == 0.25
