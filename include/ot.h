@@ -109,7 +109,29 @@ typedef struct {
   double tol_abs;         /* <= 0: unused */
   double tol_rel;         /* <= 0: unused */
   uint64_t stream;
+  int32_t algorithm;      /* ot_algorithm; 0 (OT_ALG_BDRS, Algorithm 1) unless running the ablation */
 } ot_params;
+
+/* Row-update method (App. B "Annealed Sinkhorn Detailed Comparison" and App. G "Momentum and Kernel
+ * Ablation"): every method shares Algorithm 1's column update, schedule and initialisation and
+ * differs only in the row update.
+ *   OT_ALG_BDRS         Dual (O-)BDRS (Algorithm 1): current kernel K^(lambda k + 1), momentum.
+ *   OT_ALG_AS           annealed Sinkhorn: old kernel K^(k) (K^(0) = 1), no momentum.
+ *   OT_ALG_AS_MOMENTUM  old kernel with the momentum extrapolation (v^{k-1})^2 / v^{k-2}.
+ *   OT_ALG_AS_CURRENT   current kernel K^(k+1), no momentum.
+ *   OT_ALG_DAS          debiased annealed Sinkhorn: old kernel, no momentum, numerator
+ *                       (u^{k-1})^theta_k r with theta_1 = 0, theta_k = 1/k.
+ * The ablation methods need lambda = 1 (the schedule eta/(k+1) they are defined on).  The
+ * certificate of Prop. 3 needs the row update's kernel to be the current one (its intermediate plan
+ * has row sums r only then): the old-kernel methods need cert_every = 0, and ot_certificate returns
+ * OT_EINVAL for them.  The server runs OT_ALG_BDRS only. */
+typedef enum {
+  OT_ALG_BDRS = 0,
+  OT_ALG_AS = 1,
+  OT_ALG_AS_MOMENTUM = 2,
+  OT_ALG_AS_CURRENT = 3,
+  OT_ALG_DAS = 4
+} ot_algorithm;
 
 /* Outcome of a solve or a run of steps.  U, L are the bounds of the latest certificate,
  * U_best = min_t U_t and L_best = max_t L_t over all certificates so far (App. G.3);

@@ -48,7 +48,11 @@ class OtProblem(C.Structure):
 class OtParams(C.Structure):
     _fields_ = [("eps0", C.c_double), ("lam", C.c_double), ("max_iters", C.c_int64),
                 ("time_budget_s", C.c_double), ("cert_every", C.c_int32), ("precision", C.c_int32),
-                ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("stream", C.c_uint64)]
+                ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("stream", C.c_uint64),
+                ("algorithm", C.c_int32)]
+
+
+ALGORITHMS = {"bdrs": 0, "as": 1, "as_momentum": 2, "as_current": 3, "das": 4}
 
 
 class OtResult(C.Structure):
@@ -173,7 +177,7 @@ def make_problem(x, y, a, b, cost_scale: float = 0.0, omega: float = 0.0, zero_m
 
 
 def make_params(eps0=1.0, lam=1.0, max_iters=1000, cert_every=100, precision="mufu", tol_abs=0.0,
-                tol_rel=0.0, time_budget_s=0.0, stream: int = 0) -> OtParams:
+                tol_rel=0.0, time_budget_s=0.0, stream: int = 0, algorithm="bdrs") -> OtParams:
     prm = OtParams()
     _lib.ot_params_default(C.byref(prm))
     prm.eps0 = float(eps0)
@@ -185,6 +189,7 @@ def make_params(eps0=1.0, lam=1.0, max_iters=1000, cert_every=100, precision="mu
     prm.tol_rel = float(tol_rel)
     prm.time_budget_s = float(time_budget_s)
     prm.stream = int(stream)
+    prm.algorithm = ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm)
     return prm
 
 

@@ -95,11 +95,11 @@ __global__ void weight_log_kernel(const double* __restrict__ w, int npts, double
 __global__ void repack_cols_kernel(const Inst* __restrict__ I) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= I->m) return;
-  const double eps = eps_of(I, *I->k);
+  const double inv_eps = row_inv_eps(I, *I->k);
   const double b1 = I->log_beta[j], b2 = I->log_beta_prev[j];
-  const double tn = b1 + (b1 - b2) / I->lambda;
+  const double tn = alg_momentum(I->alg) ? b1 + (b1 - b2) / I->lambda : b1;
   I->log_beta_tilde_next[j] = tn;
-  store_h(I->ypack, j, I->d, (tn - I->yn2[j] / eps) * kLog2e);
+  store_h(I->ypack, j, I->d, (tn - I->yn2[j] * inv_eps) * kLog2e);
 }
 
 // max and min of ||x_i - y_j||^2 over all pairs (FP32, one launch, any grid size).

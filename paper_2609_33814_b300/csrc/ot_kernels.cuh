@@ -18,6 +18,12 @@ enum : int { kErrTimeout = 1, kErrNonFinite = 2 };
 // Precision of one sweep launch.  The three fast modes differ only in how exp2 is evaluated:
 // MUFU, an FMA-pipe polynomial, or a fixed split between the two.
 enum : int { kSweepFast = 0, kSweepComp = 1, kSweepF64 = 2, kSweepFastPoly = 3, kSweepFastSplit = 4 };
+// Row-update methods (App. B; App. G "Momentum and Kernel Ablation"; lambda = 1 for all but BDRS):
+// the row sweep's kernel is the current K^(k+1) or the old K^(k), and its column scaling is the
+// momentum extrapolation or v^{k-1}; DAS also multiplies r by (u^{k-1})^theta_k.
+enum : int { kAlgBDRS = 0, kAlgAS = 1, kAlgASMomentum = 2, kAlgASCurrent = 3, kAlgDAS = 4 };
+__host__ __device__ constexpr bool alg_old_kernel(int a) { return a == kAlgAS || a == kAlgASMomentum || a == kAlgDAS; }
+__host__ __device__ constexpr bool alg_momentum(int a) { return a == kAlgBDRS || a == kAlgASMomentum; }
 
 __host__ __device__ constexpr bool is_fast_mode(int mode) {
   return mode == kSweepFast || mode == kSweepFastPoly || mode == kSweepFastSplit;
@@ -45,6 +51,7 @@ struct Inst {
   int nms[2][2];
   int ms_tiles[2][2];
   uint32_t wait_limit;           // mbarrier polls before a sweep gives up waiting for a tile
+  int alg;                       // row-update method (kAlg*): Dual (O-)BDRS or an ablation method
   double kappa, eta, lambda, omega;
   float* xpack;                  // [tiles_x][kNComp][kTQ]
   float* ypack;                  // [tiles_y][kNComp][kTQ]

@@ -280,6 +280,18 @@ ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q) {
     ctx.set_error("lambda must lie in [1, 2) (got %g)", q->lambda);
     return OT_EINVAL;
   }
+  if (q->algorithm < OT_ALG_BDRS || q->algorithm > OT_ALG_DAS) {
+    ctx.set_error("unknown algorithm %d", q->algorithm);
+    return OT_EINVAL;
+  }
+  if (q->algorithm != OT_ALG_BDRS && q->lambda != 1.0) {
+    ctx.set_error("the annealed-Sinkhorn ablation methods run on the lambda = 1 schedule");
+    return OT_EINVAL;
+  }
+  if (alg_old_kernel(q->algorithm) && q->cert_every != 0) {
+    ctx.set_error("certificates need a current-kernel row update: set cert_every = 0 for this algorithm");
+    return OT_EINVAL;
+  }
   if (q->max_iters < 0 || q->cert_every < 0) {
     ctx.set_error("max_iters and cert_every must be >= 0");
     return OT_EINVAL;
@@ -325,6 +337,7 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   h.d = in.d;
   h.eta = q->eps0;
   h.lambda = q->lambda;
+  h.alg = q->algorithm;
 
   const size_t n = in.n, m = in.m;
   size_t nsp = 0;
@@ -843,6 +856,10 @@ ot_status ot_certificate(ot_state* st, ot_result* res) {
   Instance& in = st->in;
   if (in.k < 1) {
     st->ctx->c.set_error("no completed iteration to certify");
+    return OT_EINVAL;
+  }
+  if (alg_old_kernel(in.h.alg)) {
+    st->ctx->c.set_error("no certificate for an old-kernel row update (Prop. 3's intermediate plan needs the current one)");
     return OT_EINVAL;
   }
   cudaSetDevice(st->ctx->c.device);

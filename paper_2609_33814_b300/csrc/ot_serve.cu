@@ -526,7 +526,7 @@ void ot_serve_destroy(ot_server* sv) {
 ot_status ot_serve_submit(ot_server* sv, const ot_problem* prob, const ot_params* params, uint64_t* req_id) {
   if (!sv || !prob || !params || !req_id) return OT_EINVAL;
   Server& S = sv->s;
-  if (params->cert_every < 1) return OT_EINVAL;
+  if (params->cert_every < 1 || params->algorithm != OT_ALG_BDRS) return OT_EINVAL;
   Request* r = new (std::nothrow) Request();
   if (!r) return OT_ENOMEM;
   r->params = *params;

@@ -75,6 +75,12 @@ __device__ __forceinline__ double eps_of(const Inst* I, long long k) {
   return I->eta / (I->lambda * (double)k + 1.0);
 }
 
+// Inverse temperature of iteration k's row sweep: 1 / eta_k with the current kernel, 1 / eta_{k-1}
+// = k / eta with the old one (lambda = 1; 0 at k = 0, where K^(0) = 1).
+__device__ __forceinline__ double row_inv_eps(const Inst* I, long long k) {
+  return alg_old_kernel(I->alg) ? (double)k / I->eta : 1.0 / eps_of(I, k);
+}
+
 // Deterministic CTA-wide sum (fixed tree order); all threads must call it.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int tid = threadIdx.x;
@@ -298,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     const int qt1 = min(qtiles, (item.ms0 + item.nms) * mst);
     const int ntl = qt1 - qt0;
     const long long kiter = s_kit[cseq & 1u];
-    const double sig = 2.0 * I->kappa * kLog2e / eps_of(I, kiter);
+    const double sig = 2.0 * I->kappa * kLog2e * (side == 0 ? row_inv_eps(I, kiter) : 1.0 / eps_of(I, kiter));
 
     // ---- thread-side points ----
     float u[R][D];
@@ -701,7 +707,10 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
                           __ldcg(&I->hint_bad[2 * side + ((kiter - 1) & 1)]) == 0;
     const double lam = I->lambda;
     const double inv_lam = 1.0 / lam;
-    const double inv_eps1 = 1.0 / eps_of(I, kiter + 1);
+    const double inv_eps1 = row_inv_eps(I, kiter + 1);  // the next row sweep's, for the column pack
+    const double inv_row = row_inv_eps(I, kiter);
+    // hints predict this side's next log-sum-exp: scale by the ratio of its temperatures
+    const double hint_ratio = side == 0 ? row_inv_eps(I, kiter + 1) / inv_row : eps / eps_of(I, kiter + 1);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     bool bad = false;
     bool hmiss = false;  // a stored hint missed this sweep's log-sum-exp by more than kHintTol
@@ -785,12 +794,13 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         const float l = (float)lse2;
         hmiss |= kiter == 0 || !(fabsf(e - l) <= kHintTol);
         bad |= use_hint && e - l > kHintGuard;  // flushed terms could matter: reject the sweep
-        hint[p] = (float)(lse2 * eps * inv_eps1);
+        hint[p] = (float)(lse2 * hint_ratio);
       }
       // state written by other CTAs of this launch (earlier phases) is read through L2
       if (side == 0) {
-        const double lse = lse2 * kLn2 - I->xn2[p] * inv_eps;
-        const double lah = I->log_a[p] - lse;
+        const double lse = lse2 * kLn2 - I->xn2[p] * inv_row;
+        double lah = I->log_a[p] - lse;
+        if (I->alg == kAlgDAS && kiter >= 2) lah += __ldcg(&I->log_alpha[p]) / (double)kiter;  // theta_k = 1/k
         bad |= !isfinite(lah);
         I->log_alpha_hat[p] = lah;
         I->log_alpha[p] = (1.0 - lam) * __ldcg(&I->log_alpha[p]) + lam * lah;
@@ -814,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           I->log_beta_prev[p] = bold;
           I->log_beta[p] = bnew;
           I->log_beta_hat[p] = lbh;
-          const double tn = bnew + (bnew - bold) * inv_lam;
+          const double tn = alg_momentum(I->alg) ? bnew + (bnew - bold) * inv_lam : bnew;
           I->log_beta_tilde_next[p] = tn;
           store_h(I->ypack, p, I->d, (tn - I->yn2[p] * inv_eps1) * kLog2e);
         } else {
