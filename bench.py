@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--cert-every", type=int, default=100)
     ap.add_argument("--tol-rel", type=float, default=0.01)
     ap.add_argument("--lam", type=float, default=1.5, help="arms workload: overrelaxation lambda")
+    ap.add_argument("--n-points", type=int, default=1 << 16, help="ablation workload: points per cloud")
+    ap.add_argument("--eta", type=float, default=0.1, help="ablation workload: eps0")
     ap.add_argument("--seed", type=int, default=2609)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--workload", default="serve", choices=["serve", "sweep", "project", "arms"],
+    ap.add_argument("--workload", default="serve", choices=["serve", "sweep", "project", "arms", "ablation"],
                     help="serve: the serving stream (the bench line); sweep: one resident instance, "
                          "fast iterations only (kernel roofline and profiling)")
     ap.add_argument("--size", type=int, default=512, help="sweep workload: s for an s x s grid, or -n for "
@@ -561,6 +563,49 @@ def run_arms(args):
     print(json.dumps(out), flush=True)
 
 
+def run_ablation(args):
+    """The row-update ablation (App. G "Momentum and Kernel Ablation") on an instance with a closed-form
+    p*: a cloud of quantised RGB colours and its translate by v (p* = kappa ||v||^2).  For each method
+    the dual lower bound L = <r, f> + <c, g> of Prop. 3 is formed from the state after each checkpoint
+    (valid for every method: its column update makes B = c / (K^T A)); reported: the relative dual gap
+    (p* - L) / p* per checkpoint and the sweep throughput."""
+    import torch
+    import paper_2609_33814_b300 as P
+    n = args.n_points
+    x = np.round(I.rgb_cloud(n, args.seed).astype(np.float64) * 1024.0) / 1024.0
+    v = np.array([52.0, -31.0, 17.0]) / 1024.0
+    y = (x + v).astype(np.float32)
+    x = x.astype(np.float32)
+    a = np.full(n, 1.0 / n)
+    kappa = 1.0 / 3.0
+    pstar = kappa * float(v @ v)
+    ctx = P.Context(0)
+    checkpoints = [50, 200, 800]
+    methods = {}
+    for alg in ("bdrs", "as", "as_momentum", "as_current", "das"):
+        S = ctx.state(x, y, a, a, cost_scale=kappa, omega=1.0, eps0=args.eta, lam=1.0, precision="mufu",
+                      cert_every=0, algorithm=alg)
+        gaps, k, tsum = {}, 0, 0.0
+        for c in checkpoints:
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            S.step(c - k)
+            torch.cuda.synchronize()
+            tsum += time.perf_counter() - t
+            k = c
+            eps = args.eta / (k - 1 + 1.0)
+            L = float(a @ (eps * S.get(P.OT_LOG_ALPHA_HAT)) + a @ (eps * (S.get(P.OT_LOG_BETA_HAT) - np.log(a))))
+            gaps[c] = (pstar - L) / pstar
+        S.close()
+        methods[alg] = {"rel_dual_gap": gaps, "entries_per_s": 2.0 * n * n * checkpoints[-1] / tsum}
+    out = {"metric": "relative dual gap (p* - L)/p* per row-update method", "value": methods["bdrs"]["rel_dual_gap"][800],
+           "unit": "relative", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 exp / f64 potentials", "data": "synthetic",
+           "config": {"workload": f"quantised RGB cloud of {n} points and its translate (p* = kappa |v|^2)",
+                      "eta": args.eta, "lambda": 1.0, "checkpoints": checkpoints}, "methods": methods}
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(args):
     """One resident instance, fast iterations only: entries/s of the sweep kernels alone."""
     import ctypes
@@ -617,6 +662,9 @@ def main():
         return
     if args.workload == "arms":
         run_arms(args)
+        return
+    if args.workload == "ablation":
+        run_ablation(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
