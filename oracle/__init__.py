@@ -25,6 +25,8 @@ against the paper by eye:
 * ``plan_diagnostics``       - barycentric projection and marginal errors of an implicit plan
                                (App. G "Implicit implementation and output"; Tables 3 and 4)
 * ``projection_sampled``     - the same projection for a sample of rows, costs on the fly
+* ``round_plan``             - rounding of an implicit plan onto the transport polytope (the
+                               Altschuler-Weed-Rigollet procedure the paper's ablation uses for f)
 
 Pins (tests that tie this oracle to something other than itself) live in
 ``tests/test_oracle_pins.py``: brute-force p* over permutations, the 1-D
@@ -492,3 +494,21 @@ def projection_sampled(rows, x, y, log_u, log_v, kappa, eps, chunk=1 << 16):
         log_rows[t] = float(log_u[i]) + m
         y_hat[t] = w @ y
     return log_rows, y_hat
+
+
+def round_plan(log_u, log_v, C, eps, r, c) -> dict:
+    """Round X = diag(u) K diag(v) onto Pi(r, c) (App. G "Momentum and Kernel Ablation" uses this to
+    evaluate f, the cost of a feasible plan): scale the rows down to at most r, then the columns down
+    to at most c, then add the rank-one correction err_r err_c^T / ||err_r||_1.  Returns the rounded
+    plan, its cost <C, Z> and the cost of X before rounding, dense FP64."""
+    X = np.exp(plan_log(log_u, log_v, C, eps))
+    r = np.asarray(r, np.float64)
+    c = np.asarray(c, np.float64)
+    X1 = X * np.minimum(r / X.sum(axis=1), 1.0)[:, None]
+    X2 = X1 * np.minimum(c / X1.sum(axis=0), 1.0)[None, :]
+    er = r - X2.sum(axis=1)
+    ec = c - X2.sum(axis=0)
+    l1 = np.abs(er).sum()
+    Z = X2 + (np.outer(er, ec) / l1 if l1 > 0 else 0.0)
+    return {"Z": Z, "cost": float((C * Z).sum()), "cost_unrounded": float((C * X).sum()),
+            "cost_scaled": float((C * X2).sum()), "err_r": er, "err_c": ec}

@@ -421,3 +421,37 @@ def test_ablation_planted_mistakes_break_the_pin():
     assert np.abs(np.log(us[5]) - np.log(us_as[5])).max() > 1e-3      # debiasing matters
     assert np.abs(np.log(us_as[5]) - np.log(us_cur[5])).max() > 1e-3  # kernel timing matters
     assert O.das_theta(0) == O.das_theta(1) == 0.0 and O.das_theta(4) == 0.25
+
+
+# ---- rounding onto the transport polytope (the f of the paper's ablation) ----
+
+def test_round_plan_is_feasible_and_bounds_pstar():
+    """The rounded plan has exactly the prescribed marginals, is nonnegative, and its cost is at least
+    p* (brute force over permutations for uniform weights); a plan already in Pi(r, c) is unchanged."""
+    rng = np.random.default_rng(2)
+    n = 6
+    x = rng.random((n, 2)); y = rng.random((n, 2))
+    C = O.cost_matrix(x, y, 1.0)
+    r = c = np.full(n, 1.0 / n)
+    pstar = O.pstar_bruteforce(C)
+    for eps in (1.0, 0.1, 0.02):
+        R = O.round_plan(rng.normal(size=n), rng.normal(size=n), C, eps, r, c)
+        Z = R["Z"]
+        assert (Z >= -1e-15).all()
+        assert np.allclose(Z.sum(1), r, atol=1e-14) and np.allclose(Z.sum(0), c, atol=1e-14)
+        assert R["cost"] >= pstar - 1e-12
+    P0 = np.outer(r, c)
+    R0 = O.round_plan(np.log(r), np.log(c), np.zeros((n, n)), 1.0, r, c)   # X = r c^T already feasible
+    assert np.allclose(R0["Z"], P0, atol=1e-15)
+
+
+def test_rank_one_correction_cost_is_separable():
+    """For C_ij = kappa ||x_i - y_j||^2 the correction's cost e_r^T C e_c expands into O(n + m) sums:
+    kappa [(sum e_r ||x||^2)(sum e_c) + (sum e_r)(sum e_c ||y||^2) - 2 <sum e_r x, sum e_c y>].
+    (The GPU rounding relies on this; here it is checked against the dense product.)"""
+    rng = np.random.default_rng(5)
+    x = rng.random((7, 3)); y = rng.random((5, 3)); kappa = 0.4
+    C = O.cost_matrix(x, y, kappa)
+    er = rng.normal(size=7); ec = rng.normal(size=5)
+    sep = kappa * ((er @ (x ** 2).sum(1)) * ec.sum() + er.sum() * (ec @ (y ** 2).sum(1)) - 2 * (er @ x) @ (ec @ y))
+    assert abs(er @ C @ ec - sep) <= 1e-12
