@@ -239,6 +239,17 @@ typedef struct {
 ot_status ot_plan_project(ot_state* st, int32_t plan, float* y_hat, double* row_sums, double* col_sums,
                           ot_marginal_errors* err);
 
+/* The cost of a feasible plan from an implicit one (the f of the paper's ablation, App. G "Momentum
+ * and Kernel Ablation", which rounds with Altschuler, Weed and Rigollet's procedure): the rows of
+ * X = diag(u) K diag(v) (plan as in ot_plan_project) are scaled down to at most r, the columns of
+ * the result down to at most c, and err_r err_c^T / |err_r|_1 is added, which puts the plan in
+ * Pi(r, c).  Nothing n x m is formed: three streaming passes (float-float exponents, compensated
+ * sums), and the cost of the rank-one correction separates for the squared-Euclidean cost.
+ * *cost_rounded = <C, rounded plan> (an upper bound on p*, valid for every ot_algorithm),
+ * *cost_unrounded = <C, X>; either may be NULL.  Temporary device memory about 40 (n + m) bytes;
+ * waits for the state's stream. */
+ot_status ot_plan_round(ot_state* st, int32_t plan, double* cost_rounded, double* cost_unrounded);
+
 /* ---------------------------------------------------------------------------------------------
  * Continuous-batching server.  Not in the paper: a serving front end for many independent solves
  * on one GPU.  ot_serve_submit copies the problem (host arrays, or device arrays when

@@ -107,6 +107,7 @@ class OtMarginalErrors(C.Structure):
 
 OT_PLAN_BEST, OT_PLAN_LATEST, OT_PLAN_INTERMEDIATE = range(3)
 _lib.ot_plan_project.argtypes = [_P, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(OtMarginalErrors)]
+_lib.ot_plan_round.argtypes = [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
 _lib.ot_serve_create.argtypes = [_P, C.c_size_t, C.c_int32, C.c_uint64, C.POINTER(_P)]
 _lib.ot_serve_submit.argtypes = [_P, C.POINTER(OtProblem), C.POINTER(OtParams), C.POINTER(C.c_uint64)]
 _lib.ot_serve_poll.argtypes = [_P, C.c_uint64, _P, _P, C.POINTER(OtResult)]
@@ -304,6 +305,12 @@ class State:
         self.ctx.check(_lib.ot_plan_project(self._h, int(plan), y_hat.ctypes.data, row.ctypes.data, col.ctypes.data,
                                             C.byref(err)), "ot_plan_project")
         return y_hat, row, col, {k: getattr(err, k) for k, _ in OtMarginalErrors._fields_}
+
+    def round_cost(self, plan: int = OT_PLAN_BEST):
+        """``ot_plan_round``: (cost of the rounded feasible plan, cost of the unrounded plan)."""
+        cr, cu = C.c_double(), C.c_double()
+        self.ctx.check(_lib.ot_plan_round(self._h, int(plan), C.byref(cr), C.byref(cu)), "ot_plan_round")
+        return cr.value, cu.value
 
     def cost(self):
         kap, om = C.c_double(), C.c_double()

@@ -51,16 +51,17 @@ struct PlanSide {
   double kappa, inv_eps;
   double* log2_sum;       // out: log2 of the point's sum of plan entries
   float* proj;            // out (row side only): np x d barycentric projection, or null
+  double* log2_cost;      // out (cost passes): log2 of sum_q ||p - q||^2 X_pq, or null
 };
 
 // Exponent in base 2 (as in the sweep kernels): log2 X_pq = rc_p + h_q + <A_p, q>, with
 // A_p = (2 kappa log2 e / eps) p and rc_p = (log scaling_p - kappa ||p||^2 / eps) log2 e.
-template <int D, bool PROJ>
+template <int D, bool PROJ, bool COST>
 __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
   __shared__ float tile[kNComp * kTQ];
   const int tid = threadIdx.x;
   const int p0 = blockIdx.x * (kThreads * kPlanR);
-  float Ah[kPlanR][D], Al[kPlanR][D];
+  float Ah[kPlanR][D], Al[kPlanR][D], pu[kPlanR][D];
   double rc[kPlanR];
   const double sig = 2.0 * s.kappa * kL2e * s.inv_eps;
 #pragma unroll
@@ -70,17 +71,19 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const float u = ok ? s.ppack[pk_idx(p, k)] : 0.0f;
+      pu[r][k] = u;
       const double A = sig * (double)u;
       Ah[r][k] = __double2float_rn(A);
       Al[r][k] = __double2float_rn(A - (double)Ah[r][k]);
     }
     rc[r] = ok ? (s.plog[p] - s.pn2[p] * s.inv_eps) * kL2e : 0.0;
   }
-  float mref[kPlanR], S[kPlanR], Sc[kPlanR], Y[kPlanR][D], Yc[kPlanR][D];
+  float mref[kPlanR], S[kPlanR], Sc[kPlanR], Y[kPlanR][D], Yc[kPlanR][D], N[kPlanR], Nc[kPlanR];
 #pragma unroll
   for (int r = 0; r < kPlanR; ++r) {
     mref[r] = 0.0f;
     S[r] = Sc[r] = 0.0f;
+    N[r] = Nc[r] = 0.0f;
 #pragma unroll
     for (int k = 0; k < D; ++k) Y[r][k] = Yc[r][k] = 0.0f;
   }
@@ -131,6 +134,8 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
             const float f = exp2_neg_int(sh);
             S[r] *= f;
             Sc[r] *= f;
+            N[r] *= f;
+            Nc[r] *= f;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
               Y[r][k] *= f;
@@ -145,19 +150,29 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
       fresh = false;
 #pragma unroll
       for (int r = 0; r < kPlanR; ++r) {
-        float cs = 0.0f, cy[D];
+        float cs = 0.0f, cn = 0.0f, cy[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) cy[k] = 0.0f;
 #pragma unroll
         for (int cc = 0; cc < kPlanCh; ++cc) {
           const float E = ex2_mufu(v[r][cc]);
           cs += E;
+          if constexpr (COST) {
+            float d2 = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              const float df = pu[r][k] - tile[k * kTQ + c0 + cc];
+              d2 = __fmaf_rn(df, df, d2);
+            }
+            cn = __fmaf_rn(d2, E, cn);
+          }
           if constexpr (PROJ) {
 #pragma unroll
             for (int k = 0; k < D; ++k) cy[k] = __fmaf_rn(E, tile[k * kTQ + c0 + cc], cy[k]);
           }
         }
         kadd(S[r], Sc[r], cs);
+        if constexpr (COST) kadd(N[r], Nc[r], cn);
         if constexpr (PROJ) {
 #pragma unroll
           for (int k = 0; k < D; ++k) kadd(Y[r][k], Yc[r][k], cy[k]);
@@ -171,6 +186,7 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
     if (p >= s.np) continue;
     const double sum = (double)S[r] - (double)Sc[r];
     s.log2_sum[p] = rc[r] + (double)mref[r] + log2(sum);
+    if constexpr (COST) s.log2_cost[p] = rc[r] + (double)mref[r] + log2((double)N[r] - (double)Nc[r]);
     if constexpr (PROJ) {
 #pragma unroll
       for (int k = 0; k < D; ++k) s.proj[(size_t)p * D + k] = (float)(((double)Y[r][k] - (double)Yc[r][k]) / sum);
@@ -262,16 +278,60 @@ __global__ void marginal_error_kernel(const double* log2_sum, const double* w, i
   *counter = 0u;
 }
 
-template <bool PROJ>
+template <bool PROJ, bool COST = false>
 cudaError_t launch_plan_sweep(const PlanSide& s, cudaStream_t st) {
   const int blocks = (s.np + kThreads * kPlanR - 1) / (kThreads * kPlanR);
   switch (s.d) {
-    case 1: plan_sweep_kernel<1, PROJ><<<blocks, kThreads, 0, st>>>(s); break;
-    case 2: plan_sweep_kernel<2, PROJ><<<blocks, kThreads, 0, st>>>(s); break;
-    case 3: plan_sweep_kernel<3, PROJ><<<blocks, kThreads, 0, st>>>(s); break;
+    case 1: plan_sweep_kernel<1, PROJ, COST><<<blocks, kThreads, 0, st>>>(s); break;
+    case 2: plan_sweep_kernel<2, PROJ, COST><<<blocks, kThreads, 0, st>>>(s); break;
+    case 3: plan_sweep_kernel<3, PROJ, COST><<<blocks, kThreads, 0, st>>>(s); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+// lu_out = lu + min(log w - ln 2 * log2_sum, 0): the scalings of diag(min(w / sums, 1)) X.
+__global__ void plan_scale_kernel(int np, const double* lu, const double* log2_sum, const double* log_w,
+                                  double* lu_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < np) lu_out[i] = lu[i] + fmin(log_w[i] - log2_sum[i] * 0.69314718055994530942, 0.0);
+}
+
+constexpr int kRoundThreads = 1024;
+
+// One side's sums for the rounding (one block, fixed order: deterministic).  With e = w - sums of
+// the rounded-down plan (sums = 2^(log2_sum + (lu_new - lu_old) log2 e) when lu_old is given), writes
+// out = {sum e ||p||^2, sum e, sum e p_0..p_2, sum |e|, kappa sum 2^log2_cost (if given),
+//        kappa sum 2^log2_cost0 (if given)}.
+__global__ void __launch_bounds__(kRoundThreads) round_sums_kernel(int np, int d, const double* w,
+                                                                   const double* log2_sum, const double* lu_new,
+                                                                   const double* lu_old, const float* pack,
+                                                                   const double* n2, double kappa,
+                                                                   const double* log2_cost,
+                                                                   const double* log2_cost0, double* out) {
+  __shared__ double red[kRoundThreads];
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < np; i += kRoundThreads) {
+    double l2 = log2_sum[i];
+    if (lu_old) l2 += (lu_new[i] - lu_old[i]) * kL2e;
+    const double e = w[i] - exp2(l2);
+    acc[0] += e * n2[i] / kappa;
+    acc[1] += e;
+    for (int k = 0; k < d; ++k) acc[2 + k] += e * (double)pack[pk_idx(i, k)];
+    acc[5] += fabs(e);
+    if (log2_cost) acc[6] += kappa * exp2(log2_cost[i]);
+    if (log2_cost0) acc[7] += kappa * exp2(log2_cost0[i]);
+  }
+  for (int q = 0; q < 8; ++q) {
+    red[threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int st = kRoundThreads / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = red[0];
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -318,12 +378,82 @@ cudaError_t plan_diagnostics(const Inst& h, int which, double eps, const double*
   plan_pack_kernel<<<(ty * kTQ + 255) / 256, 256, 0, st>>>(h.ypack, m, ty, d, lv, h.yn2, inv_eps, yp);
   plan_pack_kernel<<<(tx * kTQ + 255) / 256, 256, 0, st>>>(h.xpack, n, tx, d, lu, h.xn2, inv_eps, xp);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  PlanSide rs{n, ty, d, h.xpack, lu, h.xn2, yp, h.kappa, inv_eps, l2r, y_hat};
-  PlanSide cs{m, tx, d, h.ypack, lv, h.yn2, xp, h.kappa, inv_eps, l2c, nullptr};
+  PlanSide rs{n, ty, d, h.xpack, lu, h.xn2, yp, h.kappa, inv_eps, l2r, y_hat, nullptr};
+  PlanSide cs{m, tx, d, h.ypack, lv, h.yn2, xp, h.kappa, inv_eps, l2c, nullptr, nullptr};
   if ((e = launch_plan_sweep<true>(rs, st)) != cudaSuccess) return e;
   if ((e = launch_plan_sweep<false>(cs, st)) != cudaSuccess) return e;
   marginal_error_kernel<<<bx, kThreads, 0, st>>>(l2r, h.a, n, row, part, counter, err);
   marginal_error_kernel<<<by, kThreads, 0, st>>>(l2c, h.b, m, col, part + 3 * bx, counter + 1, err + 3);
+  return cudaGetLastError();
+}
+
+// Bytes of working memory plan_rounding needs for an n x m instance.
+size_t round_scratch_bytes(int64_t n, int64_t m) {
+  const int64_t tx = (n + kTQ - 1) / kTQ, ty = (m + kTQ - 1) / kTQ;
+  return 256 * 14 + sizeof(double) * (size_t)(6 * n + 4 * m + 32) + sizeof(float) * (size_t)((tx + ty) * kNComp * kTQ);
+}
+
+// Rounding of the plan `which` at temperature eps onto Pi(r, c) without forming it: scale the rows
+// of X down to at most r (one row pass), the columns of the result down to at most c (one column
+// pass), then add err_r err_c^T / |err_r|_1, whose cost separates for the squared-Euclidean cost:
+//   err_r^T C err_c = kappa [(sum err_r |x|^2)(sum err_c) + (sum err_r)(sum err_c |y|^2)
+//                            - 2 <sum err_r x, sum err_c y>].
+// A third (row) pass gives the scaled plan's row sums and cost.  sums (device, 16 doubles): [0..7]
+// the row-side sums of round_sums_kernel (with the rounded and the unrounded plan's costs), [8..15]
+// the column side's.
+cudaError_t plan_rounding(const Inst& h, int which, double eps, const double* f_best, const double* g_best,
+                          void* scratch, double* sums, cudaStream_t st) {
+  const int n = h.n, m = h.m, d = h.d;
+  const int tx = h.tiles_x, ty = h.tiles_y;
+  char* base = (char*)scratch;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    void* p = base + off;
+    off += bytes;
+    return p;
+  };
+  double* lu = (double*)take(sizeof(double) * n);
+  double* lu1 = (double*)take(sizeof(double) * n);
+  double* l2r = (double*)take(sizeof(double) * n);
+  double* l2cost0 = (double*)take(sizeof(double) * n);
+  double* l2r2 = (double*)take(sizeof(double) * n);
+  double* l2cost = (double*)take(sizeof(double) * n);
+  double* lv = (double*)take(sizeof(double) * m);
+  double* lv1 = (double*)take(sizeof(double) * m);
+  double* l2c = (double*)take(sizeof(double) * m);
+  double* unused = (double*)take(sizeof(double) * m);
+  (void)unused;
+  float* xp = (float*)take(sizeof(float) * (size_t)tx * kNComp * kTQ);
+  float* yp = (float*)take(sizeof(float) * (size_t)ty * kNComp * kTQ);
+  const double inv_eps = 1.0 / eps;
+  const int nm = n > m ? n : m;
+  cudaError_t e;
+  plan_logs_kernel<<<(nm + 255) / 256, 256, 0, st>>>(which, n, m, inv_eps, f_best, g_best, h.log_b,
+                                                     h.log_alpha_hat, h.log_beta_hat, h.log_beta_tilde, lu, lv);
+  // pass 1 (rows of X): row sums and cost; scale the rows down to at most r
+  plan_pack_kernel<<<(ty * kTQ + 255) / 256, 256, 0, st>>>(h.ypack, m, ty, d, lv, h.yn2, inv_eps, yp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PlanSide r1{n, ty, d, h.xpack, lu, h.xn2, yp, h.kappa, inv_eps, l2r, nullptr, l2cost0};
+  if ((e = launch_plan_sweep<false, true>(r1, st)) != cudaSuccess) return e;
+  plan_scale_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, lu, l2r, h.log_a, lu1);
+  // pass 2 (columns of the row-scaled plan): scale the columns down to at most c
+  plan_pack_kernel<<<(tx * kTQ + 255) / 256, 256, 0, st>>>(h.xpack, n, tx, d, lu1, h.xn2, inv_eps, xp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PlanSide c2{m, tx, d, h.ypack, lv, h.yn2, xp, h.kappa, inv_eps, l2c, nullptr, nullptr};
+  if ((e = launch_plan_sweep<false>(c2, st)) != cudaSuccess) return e;
+  plan_scale_kernel<<<(m + 255) / 256, 256, 0, st>>>(m, lv, l2c, h.log_b, lv1);
+  // pass 3 (rows of the scaled plan): row sums (for err_r) and cost
+  plan_pack_kernel<<<(ty * kTQ + 255) / 256, 256, 0, st>>>(h.ypack, m, ty, d, lv1, h.yn2, inv_eps, yp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  PlanSide r3{n, ty, d, h.xpack, lu1, h.xn2, yp, h.kappa, inv_eps, l2r2, nullptr, l2cost};
+  if ((e = launch_plan_sweep<false, true>(r3, st)) != cudaSuccess) return e;
+  // err_r = r - rows of the scaled plan; err_c = c - columns: the column sums of pass 2 times the
+  // column factors (lv1 - lv)
+  round_sums_kernel<<<1, kRoundThreads, 0, st>>>(n, d, h.a, l2r2, nullptr, nullptr, h.xpack, h.xn2, h.kappa,
+                                                 l2cost, l2cost0, sums);
+  round_sums_kernel<<<1, kRoundThreads, 0, st>>>(m, d, h.b, l2c, lv1, lv, h.ypack, h.yn2, h.kappa, nullptr,
+                                                 nullptr, sums + 8);
   return cudaGetLastError();
 }
 

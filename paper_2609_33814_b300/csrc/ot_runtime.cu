@@ -22,6 +22,9 @@ namespace ot {
 
 size_t sweep_smem_bytes();
 size_t plan_scratch_bytes(int64_t n, int64_t m);
+size_t round_scratch_bytes(int64_t n, int64_t m);
+cudaError_t plan_rounding(const Inst& h, int which, double eps, const double* f_best, const double* g_best,
+                          void* scratch, double* sums, cudaStream_t st);
 cudaError_t plan_diagnostics(const Inst& h, int which, double eps, const double* f_best, const double* g_best,
                              void* scratch, float* y_hat, double* row, double* col, double* err, cudaStream_t st);
 cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int iters, int grid,
@@ -970,6 +973,62 @@ ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* 
   return OT_OK;
 }
 
+// Temperature of a state's plan (see ot_plan_kind); false with the error set if there is none.
+static bool plan_eps(Context& ctx, const Instance& in, int32_t plan, double* eps) {
+  if (plan == OT_PLAN_BEST) {
+    if (in.best_iter < 0) {
+      ctx.set_error("no certificate has been computed yet");
+      return false;
+    }
+    *eps = in.h.eta / (in.h.lambda * (double)in.best_iter + 1.0);
+  } else {
+    if (in.k < 1) {
+      ctx.set_error("the state has no completed iteration");
+      return false;
+    }
+    *eps = in.h.eta / (in.h.lambda * (double)(in.k - 1) + 1.0);
+  }
+  return true;
+}
+
+ot_status ot_plan_round(ot_state* st, int32_t plan, double* cost_rounded, double* cost_unrounded) {
+  if (!st || plan < OT_PLAN_BEST || plan > OT_PLAN_INTERMEDIATE) return OT_EINVAL;
+  Context& ctx = st->ctx->c;
+  Instance& in = st->in;
+  cudaSetDevice(ctx.device);
+  double eps;
+  if (!plan_eps(ctx, in, plan, &eps)) return OT_EINVAL;
+  const size_t o_sums = (round_scratch_bytes(in.n, in.m) + 255) & ~(size_t)255;
+  const size_t bytes = o_sums + 16 * sizeof(double);
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    ctx.set_error("device allocation of %zu bytes failed", bytes);
+    return OT_ENOMEM;
+  }
+  double h[16];
+  cudaError_t e = plan_rounding(in.h, plan, eps, in.f_best, in.g_best, mem, (double*)(mem + o_sums), in.stream);
+  ctx.launches += 10;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, mem + o_sums, sizeof(h), cudaMemcpyDeviceToHost, in.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(in.stream);
+  cudaFree(mem);
+  if (e != cudaSuccess) {
+    ctx.set_error("plan rounding failed: %s", cudaGetErrorString(e));
+    return OT_ECUDA;
+  }
+  // rank-one correction err_r err_c^T / |err_r|_1 (separable cost; see plan_rounding)
+  const double kappa = in.h.kappa;
+  double corr = 0.0;
+  if (h[5] > 0.0) {
+    double cross = 0.0;
+    for (int k = 0; k < in.d; ++k) cross += h[2 + k] * h[10 + k];
+    corr = kappa * (h[0] * h[9] + h[1] * h[8] - 2.0 * cross) / h[5];
+  }
+  if (cost_rounded) *cost_rounded = h[6] + corr;
+  if (cost_unrounded) *cost_unrounded = h[7];
+  return OT_OK;
+}
+
 ot_status ot_plan_project(ot_state* st, int32_t plan, float* y_hat, double* row_sums, double* col_sums,
                           ot_marginal_errors* err) {
   if (!st || plan < OT_PLAN_BEST || plan > OT_PLAN_INTERMEDIATE) return OT_EINVAL;
@@ -977,19 +1036,7 @@ ot_status ot_plan_project(ot_state* st, int32_t plan, float* y_hat, double* row_
   Instance& in = st->in;
   cudaSetDevice(ctx.device);
   double eps;
-  if (plan == OT_PLAN_BEST) {
-    if (in.best_iter < 0) {
-      ctx.set_error("no certificate has been computed yet");
-      return OT_EINVAL;
-    }
-    eps = in.h.eta / (in.h.lambda * (double)in.best_iter + 1.0);
-  } else {
-    if (in.k < 1) {
-      ctx.set_error("the state has no completed iteration");
-      return OT_EINVAL;
-    }
-    eps = in.h.eta / (in.h.lambda * (double)(in.k - 1) + 1.0);
-  }
+  if (!plan_eps(ctx, in, plan, &eps)) return OT_EINVAL;
   const int64_t n = in.n, m = in.m;
   // one temporary allocation: working memory, then the device outputs
   const size_t o_y = (plan_scratch_bytes(n, m) + 255) & ~(size_t)255;

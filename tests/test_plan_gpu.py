@@ -102,3 +102,47 @@ def test_projection_needs_a_certificate_and_an_iteration(ctx):
     assert e.value.status == P.OT_EINVAL
     S.project(P.OT_PLAN_LATEST)
     S.close()
+
+
+@pytest.mark.parametrize("kind,s,lam", CASES)
+@pytest.mark.parametrize("plan", [0, 1, 2])
+def test_rounding_cost_parity(ctx, kind, s, lam, plan):
+    """Cost of the rounded plan (row scaling, column scaling, rank-one correction) and of the
+    unrounded one against the oracle's dense rounding, at 1e-6 relative."""
+    if kind == "grid":
+        prob = I.grid_problem(s, 33, "gaussmix", "sparse")
+    else:
+        x = I.rgb_cloud(900, 45)
+        y = I.rgb_cloud(700, 46)
+        prob = I.Problem(x, y, I.uniform_weights(900, 47), I.uniform_weights(700, 48), 1.0 / 3.0, 1.0, "ragged3")
+    a = np.maximum(prob.a, 1e-15); a = a / a.sum()
+    b = np.maximum(prob.b, 1e-15); b = b / b.sum()
+    S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, zero_mass_floor=1e-15,
+                  eps0=1.0, lam=lam, cert_every=20, precision="mufu")
+    res = S.step(40)
+    cr, cu = S.round_cost(plan)
+    lu, lv, eps = _oracle_plan(S, plan, 1.0, lam, b, res["best_iter"])
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    R = O.round_plan(lu, lv, C, eps, a, b)
+    assert abs(cu / R["cost_unrounded"] - 1) <= 1e-6
+    assert abs(cr / R["cost"] - 1) <= 1e-6, (cr, R["cost"])
+    assert cr >= res["L_best"] - 1e-12  # a feasible plan's cost bounds the dual from above
+    S.close()
+
+
+def test_rounding_bounds_pstar_for_an_old_kernel_method(ctx):
+    """Annealed Sinkhorn (no certificate available) still gets a feasible upper bound by rounding:
+    on a line it stays above the exact p* and approaches it."""
+    x = I.random_cloud(3000, 1, 61)
+    y = I.random_cloud(2500, 1, 62)
+    a, b = I.uniform_weights(3000, 63), I.uniform_weights(2500, 64)
+    pstar = O.pstar_1d(x[:, 0], a, y[:, 0], b, 1.0)
+    S = ctx.state(x, y, a, b, cost_scale=1.0, omega=1.0, eps0=1.0, cert_every=0, algorithm="as")
+    gaps = []
+    for it in (50, 450):
+        S.step(it)
+        cr, _ = S.round_cost(P.OT_PLAN_LATEST)
+        assert cr >= pstar - 1e-12
+        gaps.append(cr - pstar)
+    assert gaps[1] < gaps[0]
+    S.close()
