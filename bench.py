@@ -55,9 +55,11 @@ def parse():
     ap.add_argument("--lam", type=float, default=1.5, help="arms workload: overrelaxation lambda")
     ap.add_argument("--n-points", type=int, default=1 << 16, help="ablation workload: points per cloud")
     ap.add_argument("--eta", type=float, default=0.1, help="ablation workload: eps0")
+    ap.add_argument("--instances", type=int, default=8, help="delay workload: instance pairs")
     ap.add_argument("--seed", type=int, default=2609)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--workload", default="serve", choices=["serve", "sweep", "project", "arms", "ablation"],
+    ap.add_argument("--workload", default="serve",
+                    choices=["serve", "sweep", "project", "arms", "ablation", "delay"],
                     help="serve: the serving stream (the bench line); sweep: one resident instance, "
                          "fast iterations only (kernel roofline and profiling)")
     ap.add_argument("--size", type=int, default=512, help="sweep workload: s for an s x s grid, or -n for "
@@ -606,6 +608,60 @@ def run_ablation(args):
     print(json.dumps(out), flush=True)
 
 
+def run_delay(args):
+    """Certification delay (the paper's D(tau) = k_cert(tau) / k_oracle(tau)): for uniform-weight
+    clouds the exact p* is an assignment problem (scipy's linear_sum_assignment on the dense cost);
+    each instance runs with a certificate every 10 iterations up to 10^4 iterations, and
+    k_oracle(tau) = first certificate iteration with U_best - p* <= tau, k_cert(tau) = first with
+    U_best - L_best <= tau (additive tau on costs normalised to [0, 1])."""
+    from scipy.optimize import linear_sum_assignment
+    import paper_2609_33814_b300 as P
+    n, count, budget, every = 1024, args.instances, 10000, 10
+    taus = [1e-2, 1e-3, 1e-4]
+    ctx = P.Context(0)
+    out_methods = {}
+    for name, lam in (("bdrs", 1.0), ("obdrs_1.99", 1.99)):
+        delays = {t: [] for t in taus}
+        certified = {t: 0 for t in taus}
+        for i in range(count):
+            x = I.rgb_cloud(n, args.seed + 2 * i)[:, :2].copy()
+            y = I.rgb_cloud(n, args.seed + 2 * i + 1)[:, :2].copy()
+            C = ((x[:, None, :].astype(np.float64) - y[None, :, :]) ** 2).sum(-1)
+            kappa = 1.0 / C.max()
+            rows, cols = linear_sum_assignment(C)
+            pstar = kappa * C[rows, cols].sum() / n
+            w = np.full(n, 1.0 / n)
+            S = ctx.state(x, y, w, w, cost_scale=kappa, omega=1.0, eps0=1.0, lam=lam, precision="mufu",
+                          cert_every=every)
+            k_or = {t: None for t in taus}
+            k_ce = {t: None for t in taus}
+            k = 0
+            while k < budget and any(v is None for v in k_ce.values()):
+                res = S.step(every)
+                k += every
+                for t in taus:
+                    if k_or[t] is None and res["U_best"] - pstar <= t:
+                        k_or[t] = k
+                    if k_ce[t] is None and res["U_best"] - res["L_best"] <= t:
+                        k_ce[t] = k
+            S.close()
+            for t in taus:
+                if k_ce[t] is not None and k_or[t] is not None:
+                    delays[t].append(k_ce[t] / k_or[t])
+                    certified[t] += 1
+        out_methods[name] = {f"{t:g}": {"median_delay": float(np.median(delays[t])) if delays[t] else None,
+                                        "max_delay": float(np.max(delays[t])) if delays[t] else None,
+                                        "certified": certified[t], "of": count} for t in taus}
+    out = {"metric": "certification delay D(tau) = k_cert / k_oracle (median over instances)",
+           "value": out_methods["bdrs"]["0.01"]["median_delay"], "unit": "ratio", "n_gpus": 1, "steps": 1,
+           "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 exp / f64 potentials, compensated certificates", "data": "synthetic",
+           "config": {"workload": f"{count} pairs of 1024-point 2-D clouds (colour-mixture marginals), uniform weights",
+                      "eps0": 1.0, "cert_every": every, "budget": budget, "pstar": "exact assignment (scipy)"},
+           "methods": out_methods}
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(args):
     """One resident instance, fast iterations only: entries/s of the sweep kernels alone."""
     import ctypes
@@ -665,6 +721,9 @@ def main():
         return
     if args.workload == "ablation":
         run_ablation(args)
+        return
+    if args.workload == "delay":
+        run_delay(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
