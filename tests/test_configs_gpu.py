@@ -127,3 +127,24 @@ def test_one_dimensional_monotone_bound():
         gaps.append(res["U_best"] - res["L_best"])
     assert gaps[1] < gaps[0]
     ctx.close()
+
+
+@pytest.mark.parametrize("cls", ["uniform", "gaussmix", "cauchy", "sparse"])
+@pytest.mark.parametrize("lam", [1.0, 1.99])
+def test_certificate_and_rounding_bracket_lp_pstar(ctx, cls, lam):
+    """The GPU's certified bounds bracket the exact transport LP value (scipy HiGHS) on 12 x 12 grid
+    histograms of every class, and the rounded plan's cost is at least p*."""
+    from exact_lp import lp_pstar
+    prob = I.grid_problem(12, 22, cls, "cauchy")
+    a = np.maximum(prob.a, 1e-15); a = a / a.sum()
+    b = np.maximum(prob.b, 1e-15); b = b / b.sum()
+    pstar = lp_pstar(a, b, O.cost_matrix(prob.x, prob.y, prob.kappa))
+    S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, zero_mass_floor=1e-15,
+                  eps0=1.0, lam=lam, cert_every=50, precision="mufu")
+    res = S.step(500)
+    # 1e-6: the certificate's stated absolute accuracy in the float-float sweeps
+    assert res["L_best"] <= pstar + 1e-6 and pstar <= res["U_best"] + 1e-6, (res["L_best"], pstar, res["U_best"])
+    assert res["U_best"] - res["L_best"] < 0.05
+    f_round, _ = S.round_cost(P.OT_PLAN_BEST)
+    assert f_round >= pstar - 1e-6
+    S.close()

@@ -455,3 +455,31 @@ def test_rank_one_correction_cost_is_separable():
     er = rng.normal(size=7); ec = rng.normal(size=5)
     sep = kappa * ((er @ (x ** 2).sum(1)) * ec.sum() + er.sum() * (ec @ (y ** 2).sum(1)) - 2 * (er @ x) @ (ec @ y))
     assert abs(er @ C @ ec - sep) <= 1e-12
+
+
+# ---- exact p* for non-uniform instances (transport LP, scipy HiGHS) ----
+
+def test_lp_pstar_agrees_with_the_one_dimensional_closed_form():
+    """Two independent exact routes agree: the LP and the monotone coupling on a line."""
+    from exact_lp import lp_pstar
+    rng = np.random.default_rng(8)
+    x, y = rng.random(40), rng.random(30)
+    a, b = rng.random(40) + 0.1, rng.random(30) + 0.1
+    a, b = a / a.sum(), b / b.sum()
+    C = O.cost_matrix(x[:, None], y[:, None], 1.0)
+    assert abs(lp_pstar(a, b, C) - O.pstar_1d(x, a, y, b, 1.0)) <= 1e-9
+
+
+@pytest.mark.parametrize("cls", ["uniform", "gaussmix", "cauchy", "sparse"])
+def test_oracle_certificate_brackets_lp_pstar(cls):
+    """On non-uniform grid histograms (the sparse class floored at 1e-15) the oracle's best bounds
+    bracket the exact transport LP value, for BDRS and O-BDRS."""
+    from exact_lp import lp_pstar
+    prob = I.grid_problem(8, 21, cls, "gaussmix")
+    a = np.maximum(prob.a, 1e-15); a = a / a.sum()
+    b = np.maximum(prob.b, 1e-15); b = b / b.sum()
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    pstar = lp_pstar(a, b, C)
+    for lam in (1.0, 1.99):
+        r = O.solve(a, b, C, 1.0, lam, 300, 50, prob.omega)
+        assert r["L_best"] <= pstar + 1e-12 <= r["U_best"] + 2e-12, (cls, lam, r["L_best"], pstar, r["U_best"])
