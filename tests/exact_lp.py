@@ -9,12 +9,17 @@ from scipy.sparse import identity, kron, vstack
 
 
 def lp_pstar(a, b, C) -> float:
-    """min <C, X> over X >= 0 with X 1 = a, X^T 1 = b (a, b normalised to the same mass)."""
+    """min <C, X> over X >= 0 with X 1 = a, X^T 1 = b (a, b normalised to the same mass).
+
+    The n + m equalities have rank n + m - 1; the last one is dropped, since a total-mass mismatch of a
+    few ulps otherwise makes HiGHS's presolve declare the full system infeasible.
+    """
     C = np.asarray(C, np.float64)
     n, m = C.shape
     rows = kron(identity(n), np.ones((1, m)))
     cols = kron(np.ones((1, n)), identity(m))
-    res = linprog(C.ravel(), A_eq=vstack([rows, cols]).tocsr(), b_eq=np.concatenate([a, b]), bounds=(0, None),
-                  method="highs")
+    A_eq = vstack([rows, cols]).tocsr()[:-1]
+    b_eq = np.concatenate([a, b])[:-1]
+    res = linprog(C.ravel(), A_eq=A_eq, b_eq=b_eq, bounds=(0, None), method="highs")
     assert res.status == 0, res.message
     return float(res.fun)
