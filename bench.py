@@ -53,13 +53,17 @@ def parse():
     ap.add_argument("--cert-every", type=int, default=100)
     ap.add_argument("--tol-rel", type=float, default=0.01)
     ap.add_argument("--lam", type=float, default=1.5, help="arms workload: overrelaxation lambda")
+    ap.add_argument("--serve-lam", type=float, default=1.0, help="serve workload: overrelaxation lambda")
     ap.add_argument("--n-points", type=int, default=1 << 16, help="ablation workload: points per cloud")
     ap.add_argument("--eta", type=float, default=0.1, help="ablation workload: eps0")
     ap.add_argument("--instances", type=int, default=8, help="delay workload: instance pairs")
+    ap.add_argument("--delay-set", default="clouds", choices=["clouds", "grids"],
+                    help="delay workload: 1024-point uniform-weight clouds (exact assignment) or 16x16 grid "
+                         "histograms of the four classes (exact transport LP)")
     ap.add_argument("--seed", type=int, default=2609)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--workload", default="serve",
-                    choices=["serve", "sweep", "project", "arms", "ablation", "delay"],
+                    choices=["serve", "sweep", "project", "arms", "ablation", "delay", "load"],
                     help="serve: the serving stream (the bench line); sweep: one resident instance, "
                          "fast iterations only (kernel roofline and profiling)")
     ap.add_argument("--size", type=int, default=512, help="sweep workload: s for an s x s grid, or -n for "
@@ -150,7 +154,7 @@ def make_stream(args, rank: int):
 
 
 def solve_params(args):
-    return dict(eps0=1.0, lam=1.0, max_iters=args.max_iters, cert_every=args.cert_every, precision="mufu",
+    return dict(eps0=1.0, lam=args.serve_lam, max_iters=args.max_iters, cert_every=args.cert_every, precision="mufu",
                 tol_rel=args.tol_rel)
 
 
@@ -429,7 +433,7 @@ def run_ours(args, rank: int, world: int):
         "vs_baseline": None, "dtype": "f32 exp / f64 potentials", "data": "synthetic",
         "config": {"workload": "serving stream, mixed 32x32/64x64/128x128 grid histograms",
                    "requests": args.requests, "rate_per_s": args.rate, "max_iters": args.max_iters,
-                   "cert_every": args.cert_every, "tol_rel": args.tol_rel, "eps0": 1.0, "lambda": 1.0,
+                   "cert_every": args.cert_every, "tol_rel": args.tol_rel, "eps0": 1.0, "lambda": args.serve_lam,
                    "engine": args.engine, "seed": args.seed, "l2": "flushed between steps (256 MB write)"},
         "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
         "time_to_gap_median_s": float(np.median(ttg)), "time_to_gap_p99_s": float(np.percentile(ttg, 99)),
@@ -458,6 +462,59 @@ def run_ours(args, rank: int, world: int):
         srv.close()
     if dist:
         td.barrier()
+
+
+def run_load(args):
+    """Offered-load sweep of the serving stream, for lambda = 1 and 1.99.  The batched capacity
+    (requests/s) is the burst rate: every request of the stream submitted at t = 0, requests /
+    makespan.  Poisson streams of the same requests at 0.5, 0.8 and 1.0 times that rate then give
+    throughput (entries / makespan, wall clock from the first submission to the last result) and
+    the p50/p99 latency from arrival to result."""
+    import copy
+    import torch
+    import paper_2609_33814_b300 as P
+    ctx = P.Context(0)
+    stream = torch.cuda.Stream()
+    srv = P.Server(ctx, hbm_budget_bytes=64 << 30, max_slots=args.slots, stream=stream.cuda_stream)
+    runs = {}
+    for lam in (1.0, 1.99):
+        a2 = copy.copy(args)
+        a2.serve_lam = lam
+
+        def stream_at(rate, burst):
+            a2.rate, a2.burst = rate, burst
+            reqs, probs = make_stream(a2, 0)
+            dev = [tuple(torch.from_numpy(v).cuda() for v in (p.x, p.y, p.a, p.b)) for p in probs]
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            r = run_batched(srv, reqs, probs, dev, a2, host=False)
+            torch.cuda.synchronize()
+            return r, time.perf_counter() - t
+
+        stream_at(args.rate, True)  # warm-up: lanes, graphs, plans
+        r, wall = stream_at(args.rate, True)
+        cap = args.requests / wall
+        rows = [{"load": "burst", "rate_per_s": None, "value": r["entries"] / wall, "makespan_s": wall,
+                 "p50_latency_s": float(np.percentile(r["latency"], 50)),
+                 "p99_latency_s": float(np.percentile(r["latency"], 99)),
+                 "converged_frac": r["converged"] / args.requests}]
+        for frac in (0.5, 0.8, 1.0):
+            r, wall = stream_at(frac * cap, False)
+            rows.append({"load": frac, "rate_per_s": frac * cap, "value": r["entries"] / wall, "makespan_s": wall,
+                         "p50_latency_s": float(np.percentile(r["latency"], 50)),
+                         "p99_latency_s": float(np.percentile(r["latency"], 99)),
+                         "converged_frac": r["converged"] / args.requests})
+        runs[f"lambda_{lam:g}"] = {"capacity_req_per_s": cap, "runs": rows}
+    srv.close()
+    out = {"metric": METRIC, "value": runs["lambda_1"]["runs"][-1]["value"], "unit": UNIT, "n_gpus": 1,
+           "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 exp / f64 potentials", "data": "synthetic",
+           "config": {"workload": "serving stream at offered loads 0.5/0.8/1.0 x the burst capacity, mixed "
+                                  "32x32/64x64/128x128 grid histograms", "requests": args.requests,
+                      "max_iters": args.max_iters, "cert_every": args.cert_every, "tol_rel": args.tol_rel,
+                      "eps0": 1.0, "seed": args.seed},
+           "lambdas": runs}
+    print(json.dumps(out), flush=True)
 
 
 def run_project(args):
@@ -608,31 +665,65 @@ def run_ablation(args):
     print(json.dumps(out), flush=True)
 
 
-def run_delay(args):
-    """Certification delay (the paper's D(tau) = k_cert(tau) / k_oracle(tau)): for uniform-weight
-    clouds the exact p* is an assignment problem (scipy's linear_sum_assignment on the dense cost);
-    each instance runs with a certificate every 10 iterations up to 10^4 iterations, and
-    k_oracle(tau) = first certificate iteration with U_best - p* <= tau, k_cert(tau) = first with
-    U_best - L_best <= tau (additive tau on costs normalised to [0, 1])."""
+def transport_lp(a, b, C) -> float:
+    """Exact p* of a small non-uniform instance: the transport LP, solved by scipy's HiGHS.  The
+    n + m equalities have rank n + m - 1, so the last is dropped (a total-mass mismatch of a few
+    ulps would otherwise make the presolve declare the system infeasible)."""
+    from scipy.optimize import linprog
+    from scipy.sparse import identity, kron, vstack
+    n, m = C.shape
+    A_eq = vstack([kron(identity(n), np.ones((1, m))), kron(np.ones((1, n)), identity(m))]).tocsr()[:-1]
+    res = linprog(C.ravel(), A_eq=A_eq, b_eq=np.concatenate([a, b])[:-1], bounds=(0, None), method="highs")
+    if res.status != 0:
+        raise RuntimeError(f"transport LP: {res.message}")
+    return float(res.fun)
+
+
+def delay_instances(args):
+    """(x, y, a, b, kappa, p*) per instance pair of the delay workload, with the exact p*."""
     from scipy.optimize import linear_sum_assignment
-    import paper_2609_33814_b300 as P
-    n, count, budget, every = 1024, args.instances, 10000, 10
-    taus = [1e-2, 1e-3, 1e-4]
-    ctx = P.Context(0)
-    out_methods = {}
-    for name, lam in (("bdrs", 1.0), ("obdrs_1.99", 1.99)):
-        delays = {t: [] for t in taus}
-        certified = {t: 0 for t in taus}
-        for i in range(count):
+    out = []
+    for i in range(args.instances):
+        if args.delay_set == "clouds":
+            n = 1024
             x = I.rgb_cloud(n, args.seed + 2 * i)[:, :2].copy()
             y = I.rgb_cloud(n, args.seed + 2 * i + 1)[:, :2].copy()
             C = ((x[:, None, :].astype(np.float64) - y[None, :, :]) ** 2).sum(-1)
             kappa = 1.0 / C.max()
             rows, cols = linear_sum_assignment(C)
-            pstar = kappa * C[rows, cols].sum() / n
             w = np.full(n, 1.0 / n)
-            S = ctx.state(x, y, w, w, cost_scale=kappa, omega=1.0, eps0=1.0, lam=lam, precision="mufu",
-                          cert_every=every)
+            out.append((x, y, w, w, kappa, kappa * C[rows, cols].sum() / n))
+        else:
+            classes = I.HIST_CLASSES
+            p = I.grid_problem(16, args.seed + 2 * i, classes[i % len(classes)], classes[(i + 1) % len(classes)])
+            a = np.maximum(p.a, 1e-15)
+            a = a / a.sum()
+            b = np.maximum(p.b, 1e-15)
+            b = b / b.sum()
+            C = p.kappa * ((p.x[:, None, :].astype(np.float64) - p.y[None, :, :]) ** 2).sum(-1)
+            out.append((p.x, p.y, p.a, p.b, p.kappa, transport_lp(a, b, C)))
+    return out
+
+
+def run_delay(args):
+    """Certification delay (the paper's D(tau) = k_cert(tau) / k_oracle(tau)).  Instances: pairs of
+    uniform-weight clouds, whose exact p* is an assignment problem (scipy's linear_sum_assignment), or
+    16x16 grid histograms of the four classes (zero masses floored at 1e-15), whose exact p* is the
+    transport LP (scipy's HiGHS).  Each runs with a certificate every 10 iterations up to 10^4
+    iterations; k_oracle(tau) = first certificate iteration with U_best - p* <= tau, k_cert(tau) =
+    first with U_best - L_best <= tau (additive tau on costs normalised to [0, 1])."""
+    import paper_2609_33814_b300 as P
+    count, budget, every = args.instances, 10000, 10
+    taus = [1e-2, 1e-3, 1e-4]
+    ctx = P.Context(0)
+    insts = delay_instances(args)
+    out_methods = {}
+    for name, lam in (("bdrs", 1.0), ("obdrs_1.99", 1.99)):
+        delays = {t: [] for t in taus}
+        certified = {t: 0 for t in taus}
+        for x, y, a, b, kappa, pstar in insts:
+            S = ctx.state(x, y, a, b, cost_scale=kappa, omega=1.0, zero_mass_floor=1e-15, eps0=1.0, lam=lam,
+                          precision="mufu", cert_every=every)
             k_or = {t: None for t in taus}
             k_ce = {t: None for t in taus}
             k = 0
@@ -652,12 +743,17 @@ def run_delay(args):
         out_methods[name] = {f"{t:g}": {"median_delay": float(np.median(delays[t])) if delays[t] else None,
                                         "max_delay": float(np.max(delays[t])) if delays[t] else None,
                                         "certified": certified[t], "of": count} for t in taus}
+    if args.delay_set == "clouds":
+        workload = f"{count} pairs of 1024-point 2-D clouds (colour-mixture marginals), uniform weights"
+        exact = "exact assignment (scipy linear_sum_assignment)"
+    else:
+        workload = f"{count} pairs of 16x16 grid histograms, classes cycled over the four histogram classes"
+        exact = "exact transport LP (scipy HiGHS)"
     out = {"metric": "certification delay D(tau) = k_cert / k_oracle (median over instances)",
            "value": out_methods["bdrs"]["0.01"]["median_delay"], "unit": "ratio", "n_gpus": 1, "steps": 1,
            "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32 exp / f64 potentials, compensated certificates", "data": "synthetic",
-           "config": {"workload": f"{count} pairs of 1024-point 2-D clouds (colour-mixture marginals), uniform weights",
-                      "eps0": 1.0, "cert_every": every, "budget": budget, "pstar": "exact assignment (scipy)"},
+           "config": {"workload": workload, "eps0": 1.0, "cert_every": every, "budget": budget, "pstar": exact},
            "methods": out_methods}
     print(json.dumps(out), flush=True)
 
@@ -721,6 +817,9 @@ def main():
         return
     if args.workload == "ablation":
         run_ablation(args)
+        return
+    if args.workload == "load":
+        run_load(args)
         return
     if args.workload == "delay":
         run_delay(args)
