@@ -92,14 +92,31 @@ __global__ void weight_log_kernel(const double* __restrict__ w, int npts, double
 
 // Column pack for iteration k from log beta^{k-1}, log beta^{k-2}:
 // beta-tilde^{k-1} = beta^{k-1} + (beta^{k-1} - beta^{k-2}) / lambda (Algorithm 1 momentum).
+// It also seeds the pack offsets (Inst::goff) of iterations k and k + 1 from the first point's
+// beta-tilde and alpha; each iteration's finalisation sets those of two iterations ahead.
 __global__ void repack_cols_kernel(const Inst* __restrict__ I) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= I->m) return;
-  const double inv_eps = row_inv_eps(I, *I->k);
-  const double b1 = I->log_beta[j], b2 = I->log_beta_prev[j];
-  const double tn = alg_momentum(I->alg) ? b1 + (b1 - b2) / I->lambda : b1;
+  const long long k = *I->k;
+  const double inv_eps = row_inv_eps(I, k);
+  auto tilde = [&](int q) {
+    const double b1 = I->log_beta[q], b2 = I->log_beta_prev[q];
+    return alg_momentum(I->alg) ? b1 + (b1 - b2) / I->lambda : b1;
+  };
+  const double tn = tilde(j);
+  double gy = 0.0;
+  if (I->goff != nullptr) {
+    gy = kLog2e * tilde(0);  // every thread derives the same value from the same inputs
+    if (j == 0) {
+      const double gx = kLog2e * I->log_alpha[0];
+      for (int t = 0; t < 2; ++t) {
+        I->goff[(k + t) & 3] = gx;
+        I->goff[4 + ((k + t) & 3)] = gy;
+      }
+    }
+  }
   I->log_beta_tilde_next[j] = tn;
-  store_h(I->ypack, j, I->d, (tn - I->yn2[j] * inv_eps) * kLog2e);
+  store_h(I->ypack, j, I->d, (tn - I->yn2[j] * inv_eps) * kLog2e - gy);
 }
 
 // max and min of ||x_i - y_j||^2 over all pairs (FP32, one launch, any grid size).

@@ -81,6 +81,13 @@ struct Inst {
   // when the previous iteration of the same side had no miss.  Null: no hints.
   float* hint[2];                // row side (n floats), column side (m floats)
   int* hint_bad;                 // 4 counters
+  // Base-2 offsets G of the packed h components: a pack stores h - G and its consumer adds G back
+  // to the log-sum-exp in FP64, which is exact (LSE_q(h_q - G + z_q) = LSE_q(h_q + z_q) - G).  The
+  // log-scalings drift in gauge (alpha c, beta / c) by a constant step per iteration, so h can grow
+  // far beyond the 1/eps scale of the exponents; the offset keeps the FP32 rounding of the pack at
+  // that scale.  [side][k mod 4], side 0 the row pack, 1 the column pack, for the packs iteration k
+  // reads; null: no offsets.
+  double* goff;
   long long* k;                  // completed iterations (released by the last column epilogue)
   long long* rows;               // completed row sweeps (released by the last row epilogue)
   long long* k0;                 // k at the start of the current launch (set by the previous one)

@@ -368,7 +368,7 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   L.cnt = cv.take<unsigned>(maxblk + 4);  // point-block counters, epilogue counter, 3 scheduler counters
   L.maxblk = maxblk;
   L.blk = cv.take<double>((n + kThreads - 1) / kThreads + 3 * ((m + kThreads - 1) / kThreads));
-  L.ctrl = cv.take<double>(24);
+  L.ctrl = cv.take<double>(32);
   L.range = cv.take<unsigned>(2);
   L.inst = cv.take<Inst>(1);
   const size_t n_items = (size_t)in.fast.n_row + in.fast.n_col + in.cert.n_row + in.cert.n_col;
@@ -435,6 +435,7 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
   h.hint_bad = (int*)(ctrl + 14);  // ctrl[14..15]: four hint-miss counters (zeroed: see the k >= 1 rule)
   h.rows = (long long*)(ctrl + 16);
   h.k0 = (long long*)(ctrl + 17);
+  h.goff = ctrl + 24;  // ctrl[24..31]: pack offsets, seeded by the column repack
   in.ctrl = ctrl;
   unsigned* range = (unsigned*)(base + o_range);
   in.d_inst = (Inst*)(base + o_inst);

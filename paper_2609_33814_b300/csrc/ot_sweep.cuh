@@ -65,6 +65,12 @@ __device__ __forceinline__ void store_h(float* pack, int p, int d, double h) {
   pack[pack_idx(p, d + 1)] = lo;
 }
 
+// Offset of the pack of `side` (0 rows, 1 columns) that iteration k reads (Inst::goff).  The slot may
+// have been written earlier in the same launch, so it is read through L2.
+__device__ __forceinline__ double pack_offset(const Inst* I, int side, long long k) {
+  return I->goff != nullptr ? __ldcg(&I->goff[4 * side + (int)(k & 3)]) : 0.0;
+}
+
 // 2^e for an integer-valued e <= 0, exact; 0 below the normal range.
 __device__ __forceinline__ double pow2i(double e) {
   if (!(e > -1022.0)) return 0.0;
@@ -711,6 +717,11 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     const double inv_row = row_inv_eps(I, kiter);
     // hints predict this side's next log-sum-exp: scale by the ratio of its temperatures
     const double hint_ratio = side == 0 ? row_inv_eps(I, kiter + 1) / inv_row : eps / eps_of(I, kiter + 1);
+    // offsets of the pack this sweep read (the other side's) for this and the next iteration, and
+    // of the pack this epilogue writes
+    const double off_q = pack_offset(I, 1 - side, kiter);
+    const double off_q1 = pack_offset(I, 1 - side, kiter + 1);
+    const double off_w = side == 0 ? pack_offset(I, 0, kiter) : pack_offset(I, 1, kiter + 1);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     bool bad = false;
     bool hmiss = false;  // a stored hint missed this sweep's log-sum-exp by more than kHintTol
@@ -794,8 +805,9 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         const float l = (float)lse2;
         hmiss |= kiter == 0 || !(fabsf(e - l) <= kHintTol);
         bad |= use_hint && e - l > kHintGuard;  // flushed terms could matter: reject the sweep
-        hint[p] = (float)(lse2 * hint_ratio);
+        hint[p] = (float)((lse2 + off_q) * hint_ratio - off_q1);
       }
+      lse2 += off_q;  // the sweep ran on h - G
       // state written by other CTAs of this launch (earlier phases) is read through L2
       if (side == 0) {
         const double lse = lse2 * kLn2 - I->xn2[p] * inv_row;
@@ -804,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         bad |= !isfinite(lah);
         I->log_alpha_hat[p] = lah;
         I->log_alpha[p] = (1.0 - lam) * __ldcg(&I->log_alpha[p]) + lam * lah;
-        store_h(I->xpack, p, I->d, (lah - I->xn2[p] * inv_eps) * kLog2e);
+        store_h(I->xpack, p, I->d, (lah - I->xn2[p] * inv_eps) * kLog2e - off_w);
         if constexpr (CERT) {
           const double f = eps * lah;
           I->f_cur[p] = f;
@@ -826,7 +838,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           I->log_beta_hat[p] = lbh;
           const double tn = alg_momentum(I->alg) ? bnew + (bnew - bold) * inv_lam : bnew;
           I->log_beta_tilde_next[p] = tn;
-          store_h(I->ypack, p, I->d, (tn - I->yn2[p] * inv_eps1) * kLog2e);
+          store_h(I->ypack, p, I->d, (tn - I->yn2[p] * inv_eps1) * kLog2e - off_w);
         } else {
           lbh = __ldcg(&I->log_beta_hat[p]);
           t = __ldcg(&I->log_beta_tilde[p]);
@@ -928,6 +940,12 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         if (I->hint_bad != nullptr) {
           I->hint_bad[(kiter + 1) & 1] = 0;
           I->hint_bad[2 + ((kiter + 1) & 1)] = 0;
+        }
+        // pack offsets of iteration kiter + 2 (their slots last served iteration kiter - 2): the
+        // current values of the first point, which the drift moves by a few steps until then
+        if (I->goff != nullptr) {
+          I->goff[(kiter + 2) & 3] = kLog2e * __ldcg(&I->log_alpha_hat[0]);
+          I->goff[4 + ((kiter + 2) & 3)] = kLog2e * __ldcg(&I->log_beta_tilde_next[0]);
         }
         if (jit == iters - 1) *I->k0 = kiter + 1;  // the next launch starts here
         __threadfence();
