@@ -141,7 +141,7 @@ def combine_over_ranks(td, device, t_step, entries, e2e_t, e2e_entries):
             max(float(g[2]) for g in gathered), sum(float(g[3]) for g in gathered))
 
 
-FAST_DRAM_BYTES_PER_ENTRY = (4.668805e9 + 11.649008e9) / 4.52e11
+FAST_DRAM_BYTES_PER_ENTRY = (4.691118e9 + 11.645544e9) / 4.52e11
 
 
 def make_stream(args, rank: int):
