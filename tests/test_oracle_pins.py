@@ -483,3 +483,56 @@ def test_oracle_certificate_brackets_lp_pstar(cls):
     for lam in (1.0, 1.99):
         r = O.solve(a, b, C, 1.0, lam, 300, 50, prob.omega)
         assert r["L_best"] <= pstar + 1e-12 <= r["U_best"] + 2e-12, (cls, lam, r["L_best"], pstar, r["U_best"])
+
+
+# ---- gauge (alpha c, beta / c): equivariance of Algorithm 1 and the conserved gauge step ----
+
+def _gauge_case():
+    prob = I.grid_problem(8, 41, "gaussmix", "cauchy")
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    st = O.dual_obdrs(prob.a, prob.b, C, 1.0, 1.5, 12)
+    return prob, C, st
+
+
+def _shifted(st, c_alpha, c_beta, c_beta_prev):
+    return O.DualState(log_alpha=st.log_alpha + c_alpha, log_beta=st.log_beta + c_beta,
+                       log_beta_prev=st.log_beta_prev + c_beta_prev, log_alpha_hat=st.log_alpha_hat,
+                       log_beta_hat=st.log_beta_hat, log_beta_tilde=st.log_beta_tilde, k=st.k, eps=st.eps)
+
+
+@pytest.mark.parametrize("lam", [1.0, 1.5, 1.99])
+def test_step_is_gauge_equivariant_and_certificate_invariant(lam):
+    """A gauge c on the state (log alpha - c, log beta + c, log beta_prev + c) comes out of one
+    iteration unchanged: log alpha-hat - c, log beta-hat + c, log beta + c; Prop. 3's bounds, which
+    depend on the plan only, do not move."""
+    prob, C, st = _gauge_case()
+    la, lb = np.log(prob.a), np.log(prob.b)
+    c = 37.25
+    s0 = O.dual_obdrs_step(st, la, lb, C, 1.0, lam)
+    s1 = O.dual_obdrs_step(_shifted(st, -c, c, c), la, lb, C, 1.0, lam)
+    np.testing.assert_allclose(s1.log_alpha_hat + c, s0.log_alpha_hat, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(s1.log_beta_hat - c, s0.log_beta_hat, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(s1.log_beta - c, s0.log_beta, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(s1.log_alpha + c, s0.log_alpha, rtol=0, atol=1e-9)
+    c0 = O.certificate_of(s0, prob.a, prob.b, C, prob.omega)
+    c1 = O.certificate_of(s1, prob.a, prob.b, C, prob.omega)
+    assert abs(c0["U"] - c1["U"]) <= 1e-12 and abs(c0["L"] - c1["L"]) <= 1e-12
+
+
+@pytest.mark.parametrize("lam", [1.0, 1.99])
+def test_momentum_conserves_a_gauge_step(lam):
+    """With a gauge step v between beta^{k-2} and beta^{k-1} (log beta_prev + c, log beta + c + v),
+    the momentum term log b + (log b - log b_prev) / lam carries it on: beta^k moves by c + 2v
+    whatever lam is (c_k = 2 c_{k-1} - c_{k-2}), which is why O-BDRS log-scalings drift linearly."""
+    prob, C, st = _gauge_case()
+    la, lb = np.log(prob.a), np.log(prob.b)
+    c, v = 5.0, 3.0
+    s0 = O.dual_obdrs_step(st, la, lb, C, 1.0, lam)
+    # alpha^{k-1} only enters through the relaxation; give it the gauge the step will produce
+    s1 = O.dual_obdrs_step(_shifted(st, 0.0, c + v, c), la, lb, C, 1.0, lam)
+    t_shift = (c + v) + v / lam                       # the gauge of beta-tilde
+    np.testing.assert_allclose(s1.log_beta_hat - s0.log_beta_hat, t_shift, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(s1.log_alpha_hat - s0.log_alpha_hat, -t_shift, rtol=0, atol=1e-9)
+    expect_b = (1.0 - lam) * (c + v) + lam * t_shift  # = c + 2v
+    assert abs(expect_b - (c + 2 * v)) <= 1e-12
+    np.testing.assert_allclose(s1.log_beta - s0.log_beta, c + 2 * v, rtol=0, atol=1e-9)
