@@ -75,7 +75,8 @@ struct Inst {
   unsigned* done;                // per-instance epilogue counter
   double* blk;                   // certificate partial sums: pblk_x row blocks, then 3 per column block
   // Shift hints of the fast sweeps: per point, the base-2 log-sum-exp that point's next sweep is
-  // expected to reach (this sweep's value scaled by eps_k / eps_{k+1}), and per side and iteration
+  // expected to reach (this sweep's value scaled by eps_k / eps_{k+1}), less the offset of the pack
+  // that sweep will read (goff below), so in the units of its running shift; and per side and iteration
   // parity the count of points whose stored hint missed the exact value by more than
   // kHintTol (hint_bad[2 * side + parity]).  A sweep starts its running shifts from the hints only
   // when the previous iteration of the same side had no miss.  Null: no hints.
