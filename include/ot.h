@@ -315,8 +315,8 @@ void ot_serve_destroy(ot_server* sv);
  *     overlap on the GPU (from several host threads or streams) race and must not be made.
  *   - Accuracy: log_bt enters the FP32 exponent as it is, with no gauge offset (ot_step's sweeps
  *     subtract one), so its rounding grows with max |log_bt| (about |log_bt| * 2^-24 in log2 units).
- *     A caller whose log-scalings have drifted far from zero can pass log_bt - c and add c to the
- *     result: LSE shifts by the same constant.
+ *     A caller whose log-scalings have drifted far from zero can pass log_bt - c (c a constant, e.g.
+ *     log_bt[0]) and subtract c from the output, which then comes back as log_alpha_hat + c.
  * Returns OT_ENUMERIC if an output is non-finite. */
 #define OT_NOALLOC_MAX_POINTS 16384
 ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, const float* x, const float* y,
