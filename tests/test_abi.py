@@ -57,3 +57,15 @@ def test_python_package_fails_loudly_without_library(tmp_path):
     # the binding refuses to import when libot.so is absent (no CPU fallback exists)
     src = open(os.path.join(ROOT, "paper_2609_33814_b300", "__init__.py")).read()
     assert "raise ImportError" in src and "no CPU fallback" in src
+
+
+def test_without_a_gpu_no_context_is_created(lib):
+    """With no visible GPU the library refuses to create a context and says why: there is no CPU
+    path to fall back to."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    import paper_2609_33814_b300 as P
+    with pytest.raises(P.OTError) as ei:
+        P.Context(0)
+    assert "ot_context_create" in str(ei.value)
