@@ -64,13 +64,29 @@ def parse():
     ap.add_argument("--seed", type=int, default=2609)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--workload", default="serve",
-                    choices=["serve", "sweep", "project", "arms", "ablation", "delay", "load", "transfer"],
+                    choices=["serve", "sweep", "project", "arms", "ablation", "delay", "load", "transfer",
+                             "precision"],
                     help="serve: the serving stream (the bench line); sweep: one resident instance, "
                          "fast iterations only (kernel roofline and profiling)")
     ap.add_argument("--size", type=int, default=512, help="sweep workload: s for an s x s grid, or -n for "
                                                           "n RGB points")
     ap.add_argument("--iters", type=int, default=10, help="sweep workload: iterations per step")
     ap.add_argument("--precision", default="mufu", choices=["mufu", "comp", "fp64"])
+    ap.add_argument("--skip", type=int, default=0, help="sweep workload: untimed iterations before the warm-up")
+    ap.add_argument("--refine-on", type=float, default=0.0,
+                    help="refine_on of the fast sweeps (0: the library default, -1: off)")
+    ap.add_argument("--ttg-requests", type=int, default=64,
+                    help="time-to-gap leg: requests of the stream solved under the stop rule with --ttg-max-iters")
+    ap.add_argument("--ttg-max-iters", type=int, default=100000)
+    ap.add_argument("--cmp-n", type=int, default=4,
+                    help="time-to-gap leg: 64x64 requests also solved with the compensated exponent")
+    ap.add_argument("--no-legs", action="store_true", help="skip the time-to-gap and config-1 legs")
+    ap.add_argument("--study-n", type=int, default=6, help="precision workload: requests rerun per arm")
+    ap.add_argument("--study-base", default="0:0",
+                    help="precision workload: refine_on:refine_tol of the first pass over the stream")
+    ap.add_argument("--study-arms", default="comp,centred",
+                    help="precision workload: arms rerun on the sample (comp, centred, mufu; @ON:TOL sets the "
+                         "fast sweeps' refinement thresholds)")
     return ap.parse_args()
 
 
@@ -227,17 +243,20 @@ def flush_l2(buf):
 # ----------------------------------------------------------------------------------------------
 # reference arm / CPU baseline: the FP64 oracle on the host cores
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(args, reqs, probs, budget_s: float):
-    """The oracle as it stands (dense FP64 numpy) on a bounded sample of the stream: requests in
-    arrival order, each for up to --max-iters iterations with its certificates and stop rule,
-    until about budget_s seconds of CPU work.  Returns entries/s and what was sampled."""
+def _oracle_requests(task):
+    """One host process of the CPU baseline: the oracle as it stands (dense FP64 numpy) on its share
+    of the stream's requests, in arrival order, each for up to max_iters iterations with its
+    certificates and stop rule, until budget_s seconds have passed.  Returns (entries, seconds,
+    [n:iterations])."""
+    reqs, max_iters, cert_every, tol_rel, budget_s, max_n = task
     import oracle as O
     t0 = time.perf_counter()
     entries = 0.0
     done = []
-    for r, p in zip(reqs, probs):
-        if p.n > 4096:
-            continue  # the dense oracle needs n*m*8 bytes; the 128x128 class is left out of the sample
+    for r in reqs:
+        p = I.request_problem(r)
+        if p.n > max_n:
+            continue
         C = O.cost_matrix(p.x, p.y, p.kappa)
         a = np.maximum(p.a, 1e-15)
         a = a / a.sum()
@@ -246,47 +265,90 @@ def oracle_sample(args, reqs, probs, budget_s: float):
         st = O.DualState.initial(p.n, p.m)
         la, lb = np.log(a), np.log(b)
         k = 0
-        while k < args.max_iters:
+        while k < max_iters:
             st = O.dual_obdrs_step(st, la, lb, C, 1.0, 1.0)
             k += 1
             entries += 2.0 * p.n * p.m
-            if args.cert_every > 0 and k % args.cert_every == 0:
+            if cert_every > 0 and k % cert_every == 0:
                 cert = O.certificate_of(st, a, b, C, p.omega)
-                if (cert["U"] - cert["L"]) <= args.tol_rel * abs(cert["U"]):
+                if (cert["U"] - cert["L"]) <= tol_rel * abs(cert["U"]):
                     break
             if time.perf_counter() - t0 > budget_s:
                 break
         done.append(f"{p.n}:{k}")
+        del C
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return entries / dt, dt, done
+    return entries, time.perf_counter() - t0, done
 
 
-def oracle_threads() -> int:
-    # the oracle's work is numpy element-wise exp/log/sum over dense arrays: one host thread
-    return 1
+class OraclePool:
+    """The CPU baseline's host processes: one single-threaded oracle process per host core (spawned,
+    so that no child inherits the parent's CUDA state).  The stream's requests are independent, so
+    request i goes to process i mod W; the oracle's arithmetic is unchanged.  The 128 x 128 class
+    (a 2 GB dense cost matrix and about 8 GB of temporaries per process) is included when the host
+    has the memory for every process."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[v] = "1"
+        self.workers = max(1, os.cpu_count() or 1)
+        avail = 0
+        try:
+            with open("/proc/meminfo") as f:
+                for line in f:
+                    if line.startswith("MemAvailable:"):
+                        avail = int(line.split()[1]) * 1024
+        except OSError:
+            pass
+        self.max_n = 16384 if avail >= self.workers * (12 << 30) else 4096
+        self.pool = mp.get_context("spawn").Pool(self.workers)
+
+    def sample(self, args, reqs, budget_s: float):
+        tasks = [(reqs[w::self.workers], args.max_iters, args.cert_every, args.tol_rel, budget_s, self.max_n)
+                 for w in range(self.workers)]
+        t0 = time.perf_counter()
+        outs = self.pool.map(_oracle_requests, tasks)
+        wall = time.perf_counter() - t0
+        entries = sum(o[0] for o in outs)
+        done = [d for o in outs for d in o[2]]
+        return entries / wall, wall, done
+
+    def describe(self, budget_s: float, done) -> str:
+        sizes = {}
+        for d in done:
+            n = d.split(":")[0]
+            sizes[n] = sizes.get(n, 0) + 1
+        return (f"oracle (dense FP64 numpy) in {self.workers} spawned single-threaded processes, request i of the "
+                f"stream on process i mod {self.workers}, each for ~{budget_s:.0f} s; requests with n <= "
+                f"{self.max_n}; requests started per n: {sizes}")
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
     reqs, probs = make_stream(args, 0)
+    pool = OraclePool()
     vals = []
     for i in range(args.warmup + args.steps):
-        v, dt, done = oracle_sample(args, reqs, probs, args.cpu_sample_s)
+        v, dt, done = pool.sample(args, reqs, args.cpu_sample_s)
         if i >= args.warmup:
             vals.append((v, dt, done))
+    pool.close()
     v = statistics.median([x[0] for x in vals])
-    sample = (f"oracle (dense FP64 numpy) on the stream's requests in arrival order, n <= 4096, "
-              f"~{args.cpu_sample_s:.0f} s per step; last step covered n:iters {vals[-1][2]}")
+    sample = pool.describe(args.cpu_sample_s, vals[-1][2])
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median([x[1] for x in vals]),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": "serving stream, mixed 32x32/64x64/128x128 grid histograms",
                       "requests": args.requests, "rate_per_s": args.rate, "max_iters": args.max_iters,
                       "tol_rel": args.tol_rel, "seed": args.seed},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.workers, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -294,6 +356,114 @@ def run_reference(args, rank: int, world: int):
 # ----------------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------------
+def _oracle_config1(task):
+    """The oracle's full config-1 run (32 x 32 grid, eps0 = 1, lambda = 1, 2000 iterations, a
+    certificate every 100) in one host process: (seconds, [(k, U, L)], best f, best g)."""
+    seed, iters, cert_every = task
+    import oracle as O
+    prob = I.grid_problem(32, seed)
+    t0 = time.perf_counter()
+    C = O.cost_matrix(prob.x, prob.y, prob.kappa)
+    ro = O.solve(prob.a, prob.b, C, 1.0, 1.0, iters, cert_every, prob.omega)
+    return time.perf_counter() - t0, ro["history"], ro["best"]["f"], ro["best"]["g"]
+
+
+def run_config1(P, ctx, args, oracle_res):
+    """Config 1 on the GPU (FP64 sweeps, and FP32 with compensated certificates) beside the oracle's
+    run of the same problem: wall time and the certified bounds at every certificate."""
+    import torch
+    seed, iters, ce = args.seed, 2000, 100
+    prob = I.grid_problem(32, seed)
+    out = {"workload": "32x32 grid, uniform-random weights, eps0 = 1, lambda = 1, 2000 iterations, certificate "
+                       "every 100", "seed": seed}
+    fg = {}
+    for prec in ("fp64", "mufu"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0, lam=1.0,
+                      precision=prec, cert_every=ce)
+        hist = []
+        for _ in range(iters // ce):
+            r = S.step(ce)
+            hist.append((int(r["iters"]), r["U"], r["L"]))
+        fg[prec] = (S.get(P.OT_F_BEST), S.get(P.OT_G_BEST))
+        out[prec] = {"seconds": time.perf_counter() - t0, "U_best": r["U_best"], "L_best": r["L_best"],
+                     "gap_rel": r["gap_rel"], "best_iter": int(r["best_iter"]), "certificates": hist}
+        S.close()
+    o_s, o_hist, o_f, o_g = oracle_res
+    out["oracle"] = {"seconds": o_s, "certificates": [(int(k), u, l) for k, u, l in o_hist], "cores": 1}
+    scale = max(np.abs(o_f).max(), np.abs(o_g).max())
+    out["fp64_vs_oracle"] = {"max_abs_U_L": max(max(abs(a[1] - b[1]), abs(a[2] - b[2]))
+                                               for a, b in zip(out["fp64"]["certificates"], o_hist)),
+                             "potentials_rel": max(np.abs(fg["fp64"][0] - o_f).max(),
+                                                   np.abs(fg["fp64"][1] - o_g).max()) / scale}
+    out["fp32_vs_fp64"] = {"max_abs_U_L": max(max(abs(a[1] - b[1]), abs(a[2] - b[2]))
+                                             for a, b in zip(out["mufu"]["certificates"], out["fp64"]["certificates"])),
+                           "potentials_rel": max(np.abs(fg["mufu"][0] - fg["fp64"][0]).max(),
+                                                 np.abs(fg["mufu"][1] - fg["fp64"][1]).max()) / scale}
+    return out
+
+
+def run_time_to_gap(P, ctx, args, stream):
+    """Time to a certified relative gap under the config's stop rule (--tol-rel, a certificate every
+    --cert-every, --ttg-max-iters cap; App. G.3 best-so-far bounds): the first --ttg-requests requests
+    of the serving stream, Poisson arrivals, batched server, device-resident inputs.  Then --cmp-n of
+    its 64 x 64 requests again with the compensated exponent on every iteration, so that each of those
+    results states its FP32-exponent certified gap and iterations beside the compensated ones."""
+    import copy
+    import torch
+    a2 = copy.copy(args)
+    a2.requests, a2.max_iters, a2.burst = args.ttg_requests, args.ttg_max_iters, False
+    reqs, probs = make_stream(a2, 0)
+    dev = [tuple(torch.from_numpy(v).cuda() for v in (p.x, p.y, p.a, p.b)) for p in probs]
+    srv = P.Server(ctx, hbm_budget_bytes=64 << 30, max_slots=args.slots, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids = []
+    for r, dv in zip(reqs, dev):
+        now = time.perf_counter() - t0
+        if now < r.arrival_s:
+            time.sleep(r.arrival_s - now)
+        ids.append(srv.submit(*dv, cost_scale=probs[len(ids)].kappa, omega=probs[len(ids)].omega,
+                              zero_mass_floor=1e-15, **solve_params(a2)))
+    res = [srv.wait(i, -1.0)[2] for i in ids]
+    makespan = time.perf_counter() - t0
+    srv.close()
+    conv = [r for r in res if r["stop"] == "tol"]
+    ttg = [r["latency_s"] - r["queue_s"] for r in conv]
+    lat = [r["latency_s"] for r in res]
+    nc = {}
+    for q, r in zip(reqs, res):
+        if r["stop"] != "tol":
+            key = f"{q.s}x{q.s} {q.cls_a}/{q.cls_b}"
+            nc.setdefault(key, []).append(round(r["gap_rel"], 5))
+    out = {"requests": len(reqs), "max_iters": a2.max_iters, "tol_rel": args.tol_rel, "cert_every": args.cert_every,
+           "lambda": args.serve_lam, "rate_per_s": args.rate, "makespan_s": makespan,
+           "converged_frac": len(conv) / len(res),
+           "time_to_gap_p50_s": float(np.percentile(ttg, 50)) if ttg else None,
+           "time_to_gap_p99_s": float(np.percentile(ttg, 99)) if ttg else None,
+           "iters_to_gap_median": float(np.median([r["iters"] for r in conv])) if conv else None,
+           "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+           "not_converged_best_gaps": nc,
+           "note": "time to gap = admission to the certificate that met the stop rule, converged requests only; "
+                   "latency = arrival to result, all requests (those not converged stop at max_iters)"}
+    idx = [i for i, q in enumerate(reqs) if q.s == 64][:args.cmp_n]
+    if idx:
+        srv = P.Server(ctx, hbm_budget_bytes=64 << 30, max_slots=len(idx), stream=stream.cuda_stream)
+        cids = [srv.submit(*dev[i], cost_scale=probs[i].kappa, omega=probs[i].omega, zero_mass_floor=1e-15,
+                           **dict(solve_params(a2), precision="comp")) for i in idx]
+        cres = [srv.wait(c, -1.0)[2] for c in cids]
+        srv.close()
+        out["fp32_vs_compensated"] = [
+            {"s": reqs[i].s, "classes": f"{reqs[i].cls_a}/{reqs[i].cls_b}", "seed": reqs[i].seed,
+             "fp32": {"iters": int(res[i]["iters"]), "stop": res[i]["stop"], "gap_rel": res[i]["gap_rel"],
+                      "U_best": res[i]["U_best"], "L_best": res[i]["L_best"]},
+             "compensated": {"iters": int(c["iters"]), "stop": c["stop"], "gap_rel": c["gap_rel"],
+                             "U_best": c["U_best"], "L_best": c["L_best"]},
+             "gap_rel_diff": res[i]["gap_rel"] - c["gap_rel"]} for i, c in zip(idx, cres)]
+    return out
+
+
 def peaks_for_roofline(probe, clocks):
     # entries/clk/SM bound: min(FP32 lanes / (d + 2), MUFU ex2 lanes); d = 2 for grid workloads
     fp32 = 128.0
@@ -312,6 +482,10 @@ def run_ours(args, rank: int, world: int):
         import torch.distributed as td
         td.init_process_group("nccl")
     dev = int(os.environ.get("LOCAL_RANK", 0))
+    # the CPU baseline's spawned oracle processes (rank 0); the oracle's config-1 run starts now on one
+    # of them and overlaps the GPU work
+    pool = OraclePool() if rank == 0 else None
+    c1_async = pool.pool.apply_async(_oracle_config1, ((args.seed, 2000, 100),)) if pool and not args.no_legs else None
     torch.cuda.set_device(dev)
     ctx = P.Context(dev)
     lib = P.lib()
@@ -427,7 +601,12 @@ def run_ours(args, rank: int, world: int):
     traffic = FAST_DRAM_BYTES_PER_ENTRY * fast_e / max(fast_n, 1)
     achieved = fast_e / (fast_ms / 1e3) if fast_ms > 0 else None
     peak = peaks_for_roofline(None, clocks)
-    cpu_v, cpu_dt, cpu_done = oracle_sample(args, reqs, probs, args.cpu_sample_s)
+    legs = {}
+    if not args.no_legs:
+        legs["time_to_gap"] = run_time_to_gap(P, ctx, args, stream)
+        legs["config1"] = run_config1(P, ctx, args, c1_async.get())
+    cpu_v, cpu_dt, cpu_done = pool.sample(args, reqs, args.cpu_sample_s)
+    pool.close()
     out = {
         "metric": METRIC, "value": entries_all / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
@@ -450,14 +629,14 @@ def run_ours(args, rank: int, world: int):
                      "launches": fast_n,
                      "avg_launch_ms": fast_ms / max(fast_n, 1),
                      "peak_basis": "min(128 FP32 lanes / 4 ops, 32 MUFU ex2) per clk per SM x 148 SMs x sm_max_mhz"},
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                         "sample": f"dense FP64 numpy oracle, stream requests with n <= 4096 in arrival order, "
-                                   f"{cpu_dt:.1f} s; n:iters {cpu_done}"},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": pool.workers, "kind": "oracle",
+                         "sample": pool.describe(args.cpu_sample_s, cpu_done) + f"; {cpu_dt:.1f} s wall"},
         "e2e": {"value": e2e_entries / e2e_t, "unit": UNIT,
                 "h2d_bytes_per_step": e2e_res[-1]["h2d"], "d2h_bytes_per_step": e2e_res[-1]["d2h"]},
         "gpu_launches": int(nl.value),
         "clocks": clocks,
     }
+    out.update(legs)
     print(json.dumps(out), flush=True)
     if srv is not None:
         srv.close()
@@ -795,8 +974,91 @@ def run_delay(args):
     print(json.dumps(out), flush=True)
 
 
+def run_precision(args):
+    """The FP32 exponent of the fast iterations against a compensated one, per result (App. G,
+    "Floating-point evaluation"), on the serving stream's requests under the config's stop rule.
+
+    Every request of the stream is submitted at t = 0 in OT_EXP_MUFU with the stop rule (--tol-rel
+    certified gap, --max-iters cap) and broken down by grid size and histogram class.  A sample of
+    --study-n requests (those that did not certify first, largest grids first) is then run again
+    in each arm of --study-arms, to the same cap: ``comp`` is OT_FP32_COMP (float-float exponent on
+    every iteration, the FP64-equivalent reference), ``centred`` is OT_EXP_MUFU on the same grid
+    translated by (s - 1) / 2 (exact for integer pixel coordinates; the cost is unchanged), and
+    ``mufu`` repeats the default."""
+    import torch
+    import paper_2609_33814_b300 as P
+    ctx = P.Context(0)
+    stream = torch.cuda.Stream()
+    args.burst = True
+    reqs, probs = make_stream(args, 0)
+
+    def run_set(idx, precision, centre, refine=(0.0, 0.0)):
+        srv = P.Server(ctx, hbm_budget_bytes=64 << 30, max_slots=max(len(idx), 1), stream=stream.cuda_stream)
+        prm = dict(solve_params(args), precision=precision, refine_on=refine[0], refine_tol=refine[1])
+        t0 = time.perf_counter()
+        ids = []
+        for i in idx:
+            p = probs[i]
+            x, y = p.x, p.y
+            if centre:
+                o = np.float32(0.5 * (reqs[i].s - 1))
+                x, y = x - o, y - o
+            ids.append(srv.submit(x, y, p.a, p.b, cost_scale=p.kappa, omega=p.omega, zero_mass_floor=1e-15, **prm))
+        out = {}
+        for i, rid in zip(idx, ids):
+            f, g, res = srv.wait(rid, -1.0)
+            out[i] = {"iters": int(res["iters"]), "stop": res["stop"], "gap_rel": res["gap_rel"],
+                      "U_best": res["U_best"], "L_best": res["L_best"],
+                      "latency_s": res["latency_s"] - res["queue_s"]}
+        wall = time.perf_counter() - t0
+        srv.close()
+        return out, wall
+
+    base_refine = tuple(float(v) for v in args.study_base.split(":"))
+    base, wall0 = run_set(list(range(len(reqs))), "mufu", False, base_refine)
+    groups = {}
+    for i, r in enumerate(reqs):
+        for key in (f"s{r.s}", f"s{r.s}:{r.cls_a}/{r.cls_b}"):
+            g = groups.setdefault(key, {"count": 0, "converged": 0, "iters": [], "gap": []})
+            g["count"] += 1
+            g["converged"] += base[i]["stop"] == "tol"
+            g["iters"].append(base[i]["iters"])
+            g["gap"].append(base[i]["gap_rel"])
+    table = {k: {"count": v["count"], "converged": v["converged"], "median_iters": float(np.median(v["iters"])),
+                 "median_best_gap": float(np.median(v["gap"])), "max_best_gap": float(np.max(v["gap"]))}
+             for k, v in sorted(groups.items())}
+    order = sorted(range(len(reqs)), key=lambda i: (base[i]["stop"] == "tol", -reqs[i].s, i))
+    sample = order[:args.study_n]
+    arms = {}
+    for arm in [a for a in args.study_arms.split(",") if a]:
+        # arm names: comp, mufu, centred; a suffix @ON:TOL runs the arm with the fast sweeps'
+        # refinement thresholds refine_on = ON, refine_tol = TOL (mufu@-1:0: no refinement)
+        name, _, ref = arm.partition("@")
+        centre = name == "centred"
+        refine = tuple(float(v) for v in ref.split(":")) if ref else (0.0, 0.0)
+        res, wall = run_set(sample, "comp" if name == "comp" else "mufu", centre, refine)
+        arms[arm] = {"wall_s": wall, "results": res}
+    rows = []
+    for i in sample:
+        row = {"s": reqs[i].s, "classes": f"{reqs[i].cls_a}/{reqs[i].cls_b}", "seed": reqs[i].seed,
+               "mufu": base[i]}
+        for arm, v in arms.items():
+            row[arm] = v["results"][i]
+        rows.append(row)
+    out = {"metric": "certified relative gap and iterations to it, FP32 exponent against compensated",
+           "unit": "iterations", "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "serving stream requests, burst, mixed 32x32/64x64/128x128 grid histograms",
+                      "requests": args.requests, "max_iters": args.max_iters, "cert_every": args.cert_every,
+                      "tol_rel": args.tol_rel, "eps0": 1.0, "lambda": args.serve_lam, "seed": args.seed},
+           "stream_wall_s": wall0, "converged_frac": sum(b["stop"] == "tol" for b in base.values()) / len(reqs),
+           "by_size_class": table, "sample": rows}
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(args):
-    """One resident instance, fast iterations only: entries/s of the sweep kernels alone."""
+    """One resident instance, fast iterations only: entries/s of the sweep kernels alone, after --skip
+    untimed iterations (deep in the schedule the fast sweeps refine their dominant terms, see
+    ot_params; --refine-on -1 turns that off)."""
     import ctypes
     import torch
     import paper_2609_33814_b300 as P
@@ -805,7 +1067,10 @@ def run_sweep(args):
     lib = P.lib()
     dev = [torch.from_numpy(v).cuda() for v in (prob.x, prob.y, prob.a, prob.b)]
     S = ctx.state(*dev, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0 if args.size > 0 else 0.1,
-                  precision=args.precision, cert_every=0)
+                  precision=args.precision, cert_every=0, refine_on=args.refine_on)
+    if args.skip > 0:
+        S.step(args.skip)
+    refined0 = S.counters()["tiles_refined"]
     for _ in range(args.warmup):
         S.step(args.iters)
     clock = ClockSampler(0)
@@ -831,10 +1096,12 @@ def run_sweep(args):
            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
            "config": {"workload": f"{'grid %dx%d' % (args.size, args.size) if args.size > 0 else 'rgb %d' % -args.size}"
-                                  f" d={d}, {args.iters} iterations per step", "n": prob.n, "m": prob.m},
+                                  f" d={d}, {args.iters} iterations per step", "n": prob.n, "m": prob.m,
+                      "skip": args.skip, "refine_on": args.refine_on},
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "entries/s",
                         "frac": achieved / peak, "traffic": None, "launches": tot_n,
                         "avg_launch_ms": tot_ms / max(tot_n, 1)},
+           "tiles_refined": S.counters()["tiles_refined"] - refined0,
            "clocks": clocks}
     print(json.dumps(out), flush=True)
 
@@ -863,6 +1130,9 @@ def main():
         return
     if args.workload == "delay":
         run_delay(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

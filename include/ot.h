@@ -98,7 +98,17 @@ typedef struct {
 
 /* Algorithm 1's parameters: eps0 = eta > 0, lambda in [1, 2) (O-BDRS overrelaxation; 1 = BDRS).
  * cert_every > 0 evaluates Prop. 3 after every cert_every-th iteration; 0 never.
- * stream: a cudaStream_t to run on (0 = the context's own stream). */
+ * stream: a cudaStream_t to run on (0 = the context's own stream).
+ *
+ * Refinement (OT_EXP_MUFU only).  The FP32 exponent of the fast sweeps is a sum of terms of size
+ * ~1/eps (the scaled potential and cost), so its rounding error grows as 1/eps, to about 1e-2 in
+ * log2 units at eps ~ 1e-5 on a 128 x 128 grid.  There the rounding, re-injected every iteration,
+ * stalls the certified gap (Prop. 3's upper bound sees it through the marginal violation delta).
+ * With refinement, once the exponent's rounding bound e_fast (base 2) exceeds refine_on, each sweep
+ * evaluates again in float-float (error-free transforms, as in the certificate sweeps) the chunks
+ * of 16 points that hold a point's dominant terms, so that the terms left in FP32 carry at most
+ * about refine_tol (natural log units) of error.  refine_on = 0 and refine_tol = 0 take the
+ * defaults (2^-8 and 1e-5); refine_on < 0 turns refinement off. */
 typedef struct {
   double eps0;
   double lambda;
@@ -110,6 +120,8 @@ typedef struct {
   double tol_rel;         /* <= 0: unused */
   uint64_t stream;
   int32_t algorithm;      /* ot_algorithm; 0 (OT_ALG_BDRS, Algorithm 1) unless running the ablation */
+  double refine_on;       /* refinement threshold on the FP32 exponent's rounding (see above) */
+  double refine_tol;      /* error the unrefined terms may carry (see above) */
 } ot_params;
 
 /* Row-update method (App. B "Annealed Sinkhorn Detailed Comparison" and App. G "Momentum and Kernel
@@ -299,24 +311,29 @@ void ot_serve_destroy(ot_server* sv);
 /* ---------------------------------------------------------------------------------------------
  * Allocation-free row update.  The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory (code running under a runtime or plugin host that owns all
- * device allocations and forbids libraries from calling cudaMalloc).  It computes one row sweep
- * of Algorithm 1 at temperature eps,
- *     log_alpha_hat[i] = log_r[i] - LSE_j( log_bt[j] - kappa ||x_i - y_j||^2 / eps ),
+ * device allocations and forbids libraries from calling cudaMalloc).  It computes
+ *     log_alpha_hat[i] = log_r[i] - LSE_j( log_bt[j] - kappa ||x_i - y_j||^2 / eps )
  * with the same FP32 kernel as ot_step's fast row sweep, and allocates nothing: every buffer it
  * needs beyond its arguments lives in a fixed scratch array of about 3.2 MB inside the library,
  * which every GPU that loads the library holds until the process exits.
  *   - x (n x d floats), y (m x d floats), log_r (n doubles), log_bt (m doubles) are device inputs;
  *     log_alpha_hat (n doubles) is the device output.  1 <= n, m <= OT_NOALLOC_MAX_POINTS, d in 1..3,
- *     kappa > 0, eps > 0; anything else returns OT_EINVAL before touching the device.
+ *     kappa > 0, eps > 0 (finite); anything else returns OT_EINVAL before touching the device.
  *   - stream is a cudaStream_t (0 = the legacy default stream); the call waits for it to finish.
  *   - The first call on a device looks the scratch address up for that device (with that device
- *     current); make that first call before any stream capture.
- *   - All calls share the one scratch array, which keeps the last call's contents: calls that
- *     overlap on the GPU (from several host threads or streams) race and must not be made.
+ *     current) and queries the kernel's occupancy there; make that first call before any stream
+ *     capture.  Later calls made outside stream capture look the address up again (this allocates
+ *     nothing), so the call stays valid after the device's context is destroyed and created anew.
+ *   - All calls share the one scratch array, which keeps the last call's contents (each call clears
+ *     what must start at zero): calls that overlap on the GPU (from several host threads or
+ *     streams) race and must not be made.
+ *   - CUDA failures return OT_ECUDA; the call checks each CUDA call it makes and neither reports
+ *     nor clears an error that the caller left pending.
  *   - Accuracy: log_bt enters the FP32 exponent as it is, with no gauge offset (ot_step's sweeps
  *     subtract one), so its rounding grows with max |log_bt| (about |log_bt| * 2^-24 in log2 units).
  *     A caller whose log-scalings have drifted far from zero can pass log_bt - c (c a constant, e.g.
- *     log_bt[0]) and subtract c from the output, which then comes back as log_alpha_hat + c.
+ *     log_bt[0]): the output is then log_alpha_hat + c, so subtracting c gives log_alpha_hat for the
+ *     original log_bt.
  * Returns OT_ENUMERIC if an output is non-finite. */
 #define OT_NOALLOC_MAX_POINTS 16384
 ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, const float* x, const float* y,
@@ -340,6 +357,20 @@ ot_status ot_profile_read(ot_context* ctx, int kind, int64_t* launches, double* 
  * once.  The copies already in flight are still waited for, with the normal bound, before a sweep
  * returns.  The default is 2^26 polls (seconds). */
 ot_status ot_debug_set_wait_limit(ot_context* ctx, uint32_t polls);
+
+/* Test and measurement support (not part of the method): counters of a state's sweeps, into
+ * out[0..8] (nout >= 9):
+ *   out[0..3]  point blocks whose stored shift hint missed the sweep's exact log-sum-exp by more
+ *              than 16 (base 2): row sweeps of even / odd iterations, then column sweeps of even /
+ *              odd iterations, as last counted (a side's next sweep uses the hints only when the
+ *              previous iteration's count of that side is 0);
+ *   out[4]     warp-tiles of the fast sweeps recomputed with the exact maximum because their sum
+ *              exceeded 2^64 (cumulative since the state was created);
+ *   out[5..8]  micro-splits (partials per point) of the fast row and column sweeps, then of the
+ *              certificate row and column sweeps;
+ *   out[9]     (nout >= 10) warp-tiles of the fast sweeps whose dominant terms were evaluated again in
+ *              float-float (cumulative). */
+ot_status ot_state_counters(ot_state* st, int64_t* out, int32_t nout);
 
 /* Number of CUDA kernels this context has launched since creation or the last ot_profile_reset
  * (every node of a replayed CUDA graph counts). */

@@ -49,7 +49,7 @@ class OtParams(C.Structure):
     _fields_ = [("eps0", C.c_double), ("lam", C.c_double), ("max_iters", C.c_int64),
                 ("time_budget_s", C.c_double), ("cert_every", C.c_int32), ("precision", C.c_int32),
                 ("tol_abs", C.c_double), ("tol_rel", C.c_double), ("stream", C.c_uint64),
-                ("algorithm", C.c_int32)]
+                ("algorithm", C.c_int32), ("refine_on", C.c_double), ("refine_tol", C.c_double)]
 
 
 ALGORITHMS = {"bdrs": 0, "as": 1, "as_momentum": 2, "as_current": 3, "das": 4}
@@ -96,6 +96,7 @@ _lib.ot_certificate.argtypes = [_P, C.POINTER(OtResult)]
 _lib.ot_state_get.argtypes = [_P, C.c_int, _P, C.POINTER(C.c_int64)]
 _lib.ot_state_set.argtypes = [_P, C.c_int, _P, C.c_int64]
 _lib.ot_state_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+_lib.ot_state_counters.argtypes = [_P, C.POINTER(C.c_int64), C.c_int32]
 _lib.ot_set_tile_plan.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32]
 _lib.ot_get_tile_plan.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
 
@@ -178,7 +179,8 @@ def make_problem(x, y, a, b, cost_scale: float = 0.0, omega: float = 0.0, zero_m
 
 
 def make_params(eps0=1.0, lam=1.0, max_iters=1000, cert_every=100, precision="mufu", tol_abs=0.0,
-                tol_rel=0.0, time_budget_s=0.0, stream: int = 0, algorithm="bdrs") -> OtParams:
+                tol_rel=0.0, time_budget_s=0.0, stream: int = 0, algorithm="bdrs", refine_on: float = 0.0,
+                refine_tol: float = 0.0) -> OtParams:
     prm = OtParams()
     _lib.ot_params_default(C.byref(prm))
     prm.eps0 = float(eps0)
@@ -191,6 +193,8 @@ def make_params(eps0=1.0, lam=1.0, max_iters=1000, cert_every=100, precision="mu
     prm.time_budget_s = float(time_budget_s)
     prm.stream = int(stream)
     prm.algorithm = ALGORITHMS[algorithm] if isinstance(algorithm, str) else int(algorithm)
+    prm.refine_on = float(refine_on)
+    prm.refine_tol = float(refine_tol)
     return prm
 
 
@@ -311,6 +315,14 @@ class State:
         cr, cu = C.c_double(), C.c_double()
         self.ctx.check(_lib.ot_plan_round(self._h, int(plan), C.byref(cr), C.byref(cu)), "ot_plan_round")
         return cr.value, cu.value
+
+    def counters(self) -> dict:
+        """``ot_state_counters``: shift-hint misses, fast-sweep tile recomputes, micro-split counts."""
+        out = (C.c_int64 * 10)()
+        self.ctx.check(_lib.ot_state_counters(self._h, out, 10), "ot_state_counters")
+        v = list(out)
+        return {"hint_miss_rows": v[0:2], "hint_miss_cols": v[2:4], "tile_recomputes": v[4],
+                "splits_fast": (v[5], v[6]), "splits_cert": (v[7], v[8]), "tiles_refined": v[9]}
 
     def cost(self):
         kap, om = C.c_double(), C.c_double()

@@ -1,5 +1,6 @@
 // Set-up kernels, launch helpers and the sweep dispatch table of the solver.
 #include <cfloat>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 
@@ -16,18 +17,89 @@ SweepFn get_sweep_d3(int mode, int R, int ch, int v);
 // ---------------------------------------------------------------------------------------------
 
 // Coordinates into the tile-blocked pack (padding: coords 0, h = kPadH), kappa ||.||^2 in FP64.
+// origin (3 floats, or null) is subtracted from every coordinate first; the caller only passes one
+// for which every subtraction is exact, so the cost kappa ||x - y||^2 is unchanged.
 __global__ void pack_coords_kernel(const float* __restrict__ pts, int npts, int d, int tiles, double kappa,
-                                   float* __restrict__ pack, double* __restrict__ n2) {
+                                   float* __restrict__ pack, double* __restrict__ n2, const float* origin) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= tiles * kTQ) return;
   double s = 0.0;
   for (int k = 0; k < d; ++k) {
-    const float v = p < npts ? pts[(size_t)p * d + k] : 0.0f;
+    float v = p < npts ? pts[(size_t)p * d + k] : 0.0f;
+    if (origin != nullptr && p < npts) v = __fsub_rn(v, origin[k]);
     pack[pack_idx(p, k)] = v;
     s += (double)v * (double)v;
   }
   for (int k = d; k < kNComp; ++k) pack[pack_idx(p, k)] = (k == d && p >= npts) ? kPadH : 0.0f;
   if (p < npts) n2[p] = kappa * s;
+}
+
+// Exact centring of the two clouds (translation leaves the squared-Euclidean cost unchanged).  The
+// FP32 exponent of the fast sweeps rounds at the scale of kappa ||w||^2 / eps and of <A_p, w_q>, so
+// coordinates near the origin make it more accurate; the translation is only applied when it is
+// exact for every coordinate (integer pixel grids always are), so the cost does not change at all.
+// c[0..5]: per dimension the ordered-int encoded minimum and maximum over both clouds; c[6]: set
+// when some coordinate's difference from the midpoint is not exact in FP32; origin[0..2]: the
+// translation (zeros when none applies).
+__device__ __forceinline__ int ordered_int(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float from_ordered_int(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void centre_range_kernel(const float* __restrict__ x, int n, const float* __restrict__ y, int m, int d,
+                                    int* c) {
+  int mn[3] = {INT_MAX, INT_MAX, INT_MAX}, mx[3] = {INT_MIN, INT_MIN, INT_MIN};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+    const float* p = i < n ? x + (size_t)i * d : y + (size_t)(i - n) * d;
+    for (int k = 0; k < d; ++k) {
+      const int v = ordered_int(p[k]);
+      mn[k] = min(mn[k], v);
+      mx[k] = max(mx[k], v);
+    }
+  }
+  for (int k = 0; k < d; ++k) {
+    atomicMin(&c[2 * k], mn[k]);
+    atomicMax(&c[2 * k + 1], mx[k]);
+  }
+}
+
+__device__ __forceinline__ float centre_of(const int* c, int k) {
+  const double lo = (double)from_ordered_int(c[2 * k]), hi = (double)from_ordered_int(c[2 * k + 1]);
+  return __double2float_rn(0.5 * (lo + hi));
+}
+
+__global__ void centre_check_kernel(const float* __restrict__ x, int n, const float* __restrict__ y, int m, int d,
+                                    int* c) {
+  bool bad = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n + m; i += gridDim.x * blockDim.x) {
+    const float* p = i < n ? x + (size_t)i * d : y + (size_t)(i - n) * d;
+    for (int k = 0; k < d; ++k) {
+      const float o = centre_of(c, k);
+      const float v = p[k];
+      bad |= (double)__fsub_rn(v, o) != (double)v - (double)o;  // not exact in FP32
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&c[6], 1);
+}
+
+// Also writes rzeps: a bound on eps times the magnitude of the fast sweeps' FP32 exponent parts
+// (base 2), log2 e (3 kappa sum_k M_k^2 + 2 omega) with M_k the largest |coordinate k| after the
+// translation: kappa ||w||^2 and <A_p, w_q> eps / log2 e are at most kappa sum M_k^2 and
+// 2 kappa sum M_k^2, and the offset-relative log scalings times eps at most about 2 omega.
+__global__ void centre_origin_kernel(const int* c, int d, float* origin, double kappa, double omega,
+                                     double* rzeps) {
+  double m2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const float o = (k < d && c[6] == 0) ? centre_of(c, k) : 0.0f;
+    origin[k] = o;
+    if (k < d) {
+      const double lo = (double)from_ordered_int(c[2 * k]) - o, hi = (double)from_ordered_int(c[2 * k + 1]) - o;
+      const double M = fmax(fabs(lo), fabs(hi));
+      m2 += M * M;
+    }
+  }
+  *rzeps = 1.4426950408889634 * (3.0 * kappa * m2 + 2.0 * omega);
 }
 
 // Weight normalisation w / sum(w) with an optional floor for zero masses, and log w, in two
@@ -180,31 +252,55 @@ cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int n
   return cudaLaunchKernel((const void*)fn, dim3(grid), dim3(kThreads), args, sweep_smem_bytes(), stream);
 }
 
+// The launch helpers go through cudaLaunchKernel, which returns the status of that launch: they
+// neither read nor clear an error that an earlier call of the caller left pending.
 cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
-                               double* n2, cudaStream_t s) {
+                               double* n2, cudaStream_t s, const float* origin) {
   const int tot = tiles * kTQ;
-  pack_coords_kernel<<<(tot + 255) / 256, 256, 0, s>>>(pts, npts, d, tiles, kappa, pack, n2);
-  return cudaGetLastError();
+  void* args[] = {(void*)&pts, (void*)&npts, (void*)&d, (void*)&tiles, (void*)&kappa, (void*)&pack, (void*)&n2,
+                  (void*)&origin};
+  return cudaLaunchKernel((const void*)pack_coords_kernel, dim3((tot + 255) / 256), dim3(256), args, 0, s);
+}
+
+// The centring translation of the two clouds into origin (3 floats): zeros unless it is exact;
+// and the fast sweeps' exponent bound rzeps (centre_origin_kernel).  scratch: 7 ints, initialised here.
+cudaError_t launch_centre(const float* x, int n, const float* y, int m, int d, int* scratch, float* origin,
+                          double kappa, double omega, double* rzeps, int sms, cudaStream_t s) {
+  const int init[7] = {INT_MAX, INT_MIN, INT_MAX, INT_MIN, INT_MAX, INT_MIN, 0};
+  cudaError_t e = cudaMemcpyAsync(scratch, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  const int blocks = min((n + m + 255) / 256, sms * 4);
+  void* a1[] = {(void*)&x, (void*)&n, (void*)&y, (void*)&m, (void*)&d, (void*)&scratch};
+  if ((e = cudaLaunchKernel((const void*)centre_range_kernel, dim3(blocks), dim3(256), a1, 0, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaLaunchKernel((const void*)centre_check_kernel, dim3(blocks), dim3(256), a1, 0, s)) != cudaSuccess)
+    return e;
+  const int* c = scratch;
+  void* a2[] = {(void*)&c, (void*)&d, (void*)&origin, (void*)&kappa, (void*)&omega, (void*)&rzeps};
+  return cudaLaunchKernel((const void*)centre_origin_kernel, dim3(1), dim3(1), a2, 0, s);
 }
 
 cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw,
                              double* scratch, int* err, cudaStream_t s) {
-  weight_sum_kernel<<<(npts + kNormChunk - 1) / kNormChunk, kThreads, 0, s>>>(w, npts, floor_mass, logw, scratch,
-                                                                             err);
-  weight_log_kernel<<<(npts + 255) / 256, 256, 0, s>>>(w, npts, floor_mass, scratch, wn, logw);
-  return cudaGetLastError();
+  void* a1[] = {(void*)&w, (void*)&npts, (void*)&floor_mass, (void*)&logw, (void*)&scratch, (void*)&err};
+  cudaError_t e = cudaLaunchKernel((const void*)weight_sum_kernel, dim3((npts + kNormChunk - 1) / kNormChunk),
+                                   dim3(kThreads), a1, 0, s);
+  if (e != cudaSuccess) return e;
+  const double* sc = scratch;
+  void* a2[] = {(void*)&w, (void*)&npts, (void*)&floor_mass, (void*)&sc, (void*)&wn, (void*)&logw};
+  return cudaLaunchKernel((const void*)weight_log_kernel, dim3((npts + 255) / 256), dim3(256), a2, 0, s);
 }
 
 cudaError_t launch_repack_cols(const Inst* I, int m, cudaStream_t s) {
-  repack_cols_kernel<<<(m + 255) / 256, 256, 0, s>>>(I);
-  return cudaGetLastError();
+  void* args[] = {(void*)&I};
+  return cudaLaunchKernel((const void*)repack_cols_kernel, dim3((m + 255) / 256), dim3(256), args, 0, s);
 }
 
 cudaError_t launch_pair_cost_range(const float* x, int n, const float* y, int m, int d, unsigned* mx,
                                    unsigned* mn, int sms, cudaStream_t s) {
   const int blocks = min((n + 255) / 256, sms * 8);
-  pair_cost_range_kernel<<<blocks, 256, 0, s>>>(x, n, y, m, d, mx, mn);
-  return cudaGetLastError();
+  void* args[] = {(void*)&x, (void*)&n, (void*)&y, (void*)&m, (void*)&d, (void*)&mx, (void*)&mn};
+  return cudaLaunchKernel((const void*)pair_cost_range_kernel, dim3(blocks), dim3(256), args, 0, s);
 }
 
 }  // namespace ot

@@ -94,6 +94,16 @@ struct Inst {
   long long* k0;                 // k at the start of the current launch (set by the previous one)
   double* cert;                  // certificate record (kCertLen doubles)
   int* err;                      // error bits
+  unsigned long long* recomp;    // warp-tiles of the fast sweeps recomputed with the exact maximum
+                                 // (a tile sum above 2^64); null: not counted
+  const float* origin;           // translation the packs' coordinates carry (3 floats), or null
+  // Refinement of the fast sweeps' dominant terms (see the sweep kernel): rzeps bounds eps times the
+  // magnitude of the FP32 exponent's parts (base 2; written at set-up), refine_on the FP32 rounding
+  // (base 2) above which it applies, refine_tol the error (natural log units) the unrefined terms
+  // may carry; refined counts warp-tiles evaluated again.  rzeps null or refine_on <= 0: off.
+  const double* rzeps;
+  double refine_on, refine_tol;
+  unsigned long long* refined;
 };
 
 // Split partial of the FP64 sweep: (shift, sum, cost-weighted sum, unused).

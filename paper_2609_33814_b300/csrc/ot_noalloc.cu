@@ -2,6 +2,7 @@
 // (for example code running inside a memory-capped plugin or a runtime that owns every device
 // allocation and forbids cudaMalloc from libraries).  Everything the sweep needs beyond the
 // caller's inputs and output lives in one fixed-size scratch array in this file's device memory.
+#include <cmath>
 #include <cstdint>
 #include <mutex>
 
@@ -12,7 +13,7 @@
 namespace ot {
 
 cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
-                               double* n2, cudaStream_t s);
+                               double* n2, cudaStream_t s, const float* origin);
 cudaError_t launch_repack_cols(const Inst* I, int m, cudaStream_t s);
 size_t sweep_smem_bytes();
 
@@ -41,8 +42,9 @@ constexpr size_t kScratchBytes = kOffItems + align256((size_t)kMaxBlocks * kMaxS
 
 }  // namespace
 
-// The scratch array.  Host code must not use its name as a device address: the address comes from
-// cudaGetSymbolAddress, once per device.
+// The scratch array.  Host code must not use its name as a device address (in host code it names a
+// host-side stand-in): the address comes from cudaGetSymbolAddress in device_setup below, with the
+// device current.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 // Writes the instance descriptor (passed by value) and the work items into the scratch.
@@ -52,8 +54,42 @@ __global__ void noalloc_setup_kernel(Inst inst, Inst* dst, Item* items, int pblk
   if (i < pblks * splits) items[i] = Item{0, 0, i % pblks, i / pblks, 1};
 }
 
+// Per-device set-up: the scratch address (looked up with the device current) and the launch
+// shape of the sweep kernel.  The address is looked up again on every call made outside stream
+// capture, so a context that was torn down and created again (whose module, and hence the array,
+// may have moved) never sees a stale address; the SM count and occupancy are fixed per device.
+struct DeviceSetup {
+  void* base = nullptr;
+  int resident[4] = {0, 0, 0, 0};  // per d: CTAs of the sweep kernel resident on the device (0: not yet)
+};
 static std::mutex g_mu;
-static void* g_base[256];  // scratch address per device ordinal, set on the first call
+static DeviceSetup g_dev[256];
+
+static cudaError_t device_setup(int dev, int d, cudaStream_t s, SweepFn fn, void** base, int* resident) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DeviceSetup& D = g_dev[dev];
+  if (cap == cudaStreamCaptureStatusNone || D.base == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (p == nullptr) return cudaErrorInvalidSymbol;
+    D.base = p;
+  }
+  if (D.resident[d] == 0) {
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads, sweep_smem_bytes());
+    if (e != cudaSuccess) return e;
+    D.resident[d] = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  }
+  *base = D.base;
+  *resident = D.resident[d];
+  return cudaSuccess;
+}
 
 }  // namespace ot
 
@@ -64,32 +100,24 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
                                            double* log_alpha_hat, uint64_t stream) {
   if (n < 1 || m < 1 || n > kMaxPts || m > kMaxPts) return OT_EINVAL;  // beyond the scratch capacity
   if (d < 1 || d > 3 || !x || !y || !log_r || !log_bt || !log_alpha_hat) return OT_EINVAL;
-  if (!(kappa > 0.0) || !(eps > 0.0)) return OT_EINVAL;
+  if (!(kappa > 0.0) || !(eps > 0.0) || !std::isfinite(kappa) || !std::isfinite(eps)) return OT_EINVAL;
+  // Every CUDA call below is checked where it is made, and kernels are launched with
+  // cudaLaunchKernel, which returns the launch's own status: an error that the caller left
+  // pending is neither reported here nor cleared.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return OT_ECUDA;
-  char* base;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_base[dev]) {
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        cudaGetLastError();
-        return OT_ECUDA;
-      }
-      g_base[dev] = p;
-    }
-    base = (char*)g_base[dev];
-  }
   cudaStream_t s = (cudaStream_t)(uintptr_t)stream;
+  SweepFn fn = get_sweep(d, kSweepFast, 1, 16, 0);
+  if (fn == nullptr) return OT_EINVAL;
+  char* base = nullptr;
+  int resident = 0;
+  {
+    void* b = nullptr;
+    if (device_setup(dev, d, s, fn, &b, &resident) != cudaSuccess) return OT_ECUDA;
+    base = (char*)b;
+  }
   const int tiles_x = (int)((n + kTQ - 1) / kTQ), tiles_y = (int)((m + kTQ - 1) / kTQ);
   const int pblks = (int)((n + kThreads - 1) / kThreads);  // R = 1
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  SweepFn fn = get_sweep(d, kSweepFast, 1, 16, 0);
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, kThreads, sweep_smem_bytes());
-  const int resident = (per_sm > 0 ? per_sm : 1) * sms;
   int splits = (4 * resident + pblks - 1) / pblks;
   splits = splits < 1 ? 1 : (splits > kMaxSplits ? kMaxSplits : splits);
   if (splits > tiles_y) splits = tiles_y;
@@ -141,11 +169,16 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
       cudaMemsetAsync(ctrl, 0, 24 * sizeof(double), s) != cudaSuccess ||
       cudaMemsetAsync(h.log_alpha, 0, n * sizeof(double), s) != cudaSuccess)
     return OT_ECUDA;
-  const int nitems = pblks * splits;
-  noalloc_setup_kernel<<<(nitems + 255) / 256, 256, 0, s>>>(h, d_inst, d_items, pblks, splits);
-  if (cudaGetLastError() != cudaSuccess) return OT_ECUDA;
-  if (launch_pack_coords(x, (int)n, d, tiles_x, kappa, h.xpack, (double*)h.xn2, s) != cudaSuccess ||
-      launch_pack_coords(y, (int)m, d, tiles_y, kappa, h.ypack, (double*)h.yn2, s) != cudaSuccess ||
+  int nitems = pblks * splits;
+  {
+    int pb = pblks, sp = splits;
+    void* args[] = {(void*)&h, (void*)&d_inst, (void*)&d_items, (void*)&pb, (void*)&sp};
+    if (cudaLaunchKernel((const void*)noalloc_setup_kernel, dim3((nitems + 255) / 256), dim3(256), args, 0, s) !=
+        cudaSuccess)
+      return OT_ECUDA;
+  }
+  if (launch_pack_coords(x, (int)n, d, tiles_x, kappa, h.xpack, (double*)h.xn2, s, nullptr) != cudaSuccess ||
+      launch_pack_coords(y, (int)m, d, tiles_y, kappa, h.ypack, (double*)h.yn2, s, nullptr) != cudaSuccess ||
       launch_repack_cols(d_inst, (int)m, s) != cudaSuccess)
     return OT_ECUDA;
   const int grid = nitems < resident ? nitems : resident;

@@ -52,6 +52,7 @@ struct PlanSide {
   double* log2_sum;       // out: log2 of the point's sum of plan entries
   float* proj;            // out (row side only): np x d barycentric projection, or null
   double* log2_cost;      // out (cost passes): log2 of sum_q ||p - q||^2 X_pq, or null
+  const float* origin;    // translation of the packs' coordinates, added back to proj (or null)
 };
 
 // Exponent in base 2 (as in the sweep kernels): log2 X_pq = rc_p + h_q + <A_p, q>, with
@@ -189,7 +190,9 @@ __global__ void __launch_bounds__(kThreads) plan_sweep_kernel(PlanSide s) {
     if constexpr (COST) s.log2_cost[p] = rc[r] + (double)mref[r] + log2((double)N[r] - (double)Nc[r]);
     if constexpr (PROJ) {
 #pragma unroll
-      for (int k = 0; k < D; ++k) s.proj[(size_t)p * D + k] = (float)(((double)Y[r][k] - (double)Yc[r][k]) / sum);
+      for (int k = 0; k < D; ++k)
+        s.proj[(size_t)p * D + k] =
+            (float)(((double)Y[r][k] - (double)Yc[r][k]) / sum + (s.origin != nullptr ? (double)s.origin[k] : 0.0));
     }
   }
 }
@@ -378,7 +381,7 @@ cudaError_t plan_diagnostics(const Inst& h, int which, double eps, const double*
   plan_pack_kernel<<<(ty * kTQ + 255) / 256, 256, 0, st>>>(h.ypack, m, ty, d, lv, h.yn2, inv_eps, yp);
   plan_pack_kernel<<<(tx * kTQ + 255) / 256, 256, 0, st>>>(h.xpack, n, tx, d, lu, h.xn2, inv_eps, xp);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  PlanSide rs{n, ty, d, h.xpack, lu, h.xn2, yp, h.kappa, inv_eps, l2r, y_hat, nullptr};
+  PlanSide rs{n, ty, d, h.xpack, lu, h.xn2, yp, h.kappa, inv_eps, l2r, y_hat, nullptr, h.origin};
   PlanSide cs{m, tx, d, h.ypack, lv, h.yn2, xp, h.kappa, inv_eps, l2c, nullptr, nullptr};
   if ((e = launch_plan_sweep<true>(rs, st)) != cudaSuccess) return e;
   if ((e = launch_plan_sweep<false>(cs, st)) != cudaSuccess) return e;

@@ -30,7 +30,9 @@ cudaError_t plan_diagnostics(const Inst& h, int which, double eps, const double*
 cudaError_t launch_sweep(SweepFn fn, const Inst* insts, const Item* items, int nitems, int iters, int grid,
                          unsigned* sched, cudaStream_t stream);
 cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, double kappa, float* pack,
-                               double* n2, cudaStream_t s);
+                               double* n2, cudaStream_t s, const float* origin);
+cudaError_t launch_centre(const float* x, int n, const float* y, int m, int d, int* scratch, float* origin,
+                          double kappa, double omega, double* rzeps, int sms, cudaStream_t s);
 cudaError_t launch_normalise(const double* w, int npts, double floor_mass, double* wn, double* logw,
                              double* scratch, int* err, cudaStream_t s);
 cudaError_t launch_repack_cols(const Inst* I, int m, cudaStream_t s);
@@ -253,6 +255,18 @@ int sweep_mode_of(int precision) {
   return kSweepFast;
 }
 
+// Refinement of the fast sweeps' dominant terms (OT_EXP_MUFU; see ot_params): on when the FP32
+// exponent's rounding bound (base 2) exceeds refine_on, with refine_tol the error the unrefined
+// terms may carry; 0 takes the default, refine_on < 0 turns it off (*on = 0 here).
+constexpr double kRefineOnDefault = 0x1p-8;
+constexpr double kRefineTolDefault = 1e-5;
+void refine_policy(const ot_params* q, double* on, double* tol) {
+  *on = 0.0;
+  *tol = q->refine_tol > 0.0 ? q->refine_tol : kRefineTolDefault;
+  if (q->precision != OT_EXP_MUFU || q->refine_on < 0.0) return;
+  *on = q->refine_on > 0.0 ? q->refine_on : kRefineOnDefault;
+}
+
 ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q) {
   if (!p || !q) {
     ctx.set_error("null problem or params");
@@ -273,6 +287,10 @@ ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q) {
   if (!(p->cost_scale >= 0.0) || !std::isfinite(p->cost_scale) || !(p->omega >= 0.0) || !std::isfinite(p->omega) ||
       !(p->zero_mass_floor >= 0.0)) {
     ctx.set_error("cost_scale, omega and zero_mass_floor must be finite and >= 0");
+    return OT_EINVAL;
+  }
+  if (!std::isfinite(q->refine_on) || !(q->refine_tol >= 0.0) || !std::isfinite(q->refine_tol)) {
+    ctx.set_error("refine_on and refine_tol must be finite (refine_tol >= 0)");
     return OT_EINVAL;
   }
   if (!(q->eps0 > 0.0) || !std::isfinite(q->eps0)) {
@@ -319,6 +337,7 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   in.stream = stream;
   in.sweep_mode = sweep_mode_of(q->precision);
   in.cert_mode = q->precision == OT_FP64 ? kSweepF64 : kSweepComp;
+  refine_policy(q, &in.refine_on, &in.refine_tol);
   plan_launch(ctx, in, in.sweep_mode, in.fast);
   plan_launch(ctx, in, in.cert_mode, in.cert);
   Inst& h = in.h;
@@ -368,7 +387,7 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   L.cnt = cv.take<unsigned>(maxblk + 4);  // point-block counters, epilogue counter, 3 scheduler counters
   L.maxblk = maxblk;
   L.blk = cv.take<double>((n + kThreads - 1) / kThreads + 3 * ((m + kThreads - 1) / kThreads));
-  L.ctrl = cv.take<double>(32);
+  L.ctrl = cv.take<double>(40);  // see instance_setup for the slots
   L.range = cv.take<unsigned>(2);
   L.inst = cv.take<Inst>(1);
   const size_t n_items = (size_t)in.fast.n_row + in.fast.n_col + in.cert.n_row + in.cert.n_col;
@@ -435,6 +454,7 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
   h.hint_bad = (int*)(ctrl + 14);  // ctrl[14..15]: four hint-miss counters (zeroed: see the k >= 1 rule)
   h.rows = (long long*)(ctrl + 16);
   h.k0 = (long long*)(ctrl + 17);
+  h.recomp = (unsigned long long*)(ctrl + 18);  // ctrl[18]: tile recomputes of the fast sweeps
   h.goff = ctrl + 24;  // ctrl[24..31]: pack offsets, seeded by the column repack
   in.ctrl = ctrl;
   unsigned* range = (unsigned*)(base + o_range);
@@ -481,12 +501,23 @@ ot_status instance_setup(Context& ctx, Instance& in, const ot_problem* p) {
   in.kappa = kappa;
   in.omega = omega;
 
-  OT_CUDA(launch_pack_coords(in.xraw, (int)n, in.d, h.tiles_x, kappa, h.xpack, (double*)h.xn2, s));
-  OT_CUDA(launch_pack_coords(in.yraw, (int)m, in.d, h.tiles_y, kappa, h.ypack, (double*)h.yn2, s));
+  // ctrl[32..35]: scratch of the exact centring; ctrl[36..37]: its translation (3 floats, zeros when
+  // it would not be exact), which the packs subtract and the barycentric projection adds back;
+  // ctrl[38]: the exponent bound of the fast sweeps' refinement; ctrl[39]: refined warp-tiles
+  float* origin = (float*)(ctrl + 36);
+  h.origin = origin;
+  h.rzeps = ctrl + 38;
+  h.refined = (unsigned long long*)(ctrl + 39);
+  h.refine_on = in.refine_on;
+  h.refine_tol = in.refine_tol;
+  OT_CUDA(launch_centre(in.xraw, (int)n, in.yraw, (int)m, in.d, (int*)(ctrl + 32), origin, kappa, omega, ctrl + 38,
+                        ctx.sms, s));
+  OT_CUDA(launch_pack_coords(in.xraw, (int)n, in.d, h.tiles_x, kappa, h.xpack, (double*)h.xn2, s, h.origin));
+  OT_CUDA(launch_pack_coords(in.yraw, (int)m, in.d, h.tiles_y, kappa, h.ypack, (double*)h.yn2, s, h.origin));
   // ctrl[10..13]: scratch of the two normalisations (total, arrival counter), zeroed above
   OT_CUDA(launch_normalise(ain, (int)n, p->zero_mass_floor, (double*)h.a, (double*)h.log_a, ctrl + 10, h.err, s));
   OT_CUDA(launch_normalise(bin, (int)m, p->zero_mass_floor, (double*)h.b, (double*)h.log_b, ctrl + 12, h.err, s));
-  ctx.launches += 6;
+  ctx.launches += 9;
 
   std::vector<Item> items;
   for (const LaunchPlan* pl : {&in.fast, &in.cert}) {
@@ -613,20 +644,16 @@ static ot_status issue_chunk(Context& ctx, Instance& in, int64_t count, bool cer
   if (prof) {
     OT_CUDA(cudaStreamSynchronize(in.stream));
     const double entries = 2.0 * (double)in.n * (double)in.m;  // row and column sweep
-    float ms_f = 0, ms_c = 0;
-    OT_CUDA(cudaEventElapsedTime(&ms_f, (*evs)[0], (*evs)[1]));
-    OT_CUDA(cudaEventElapsedTime(&ms_c, (*evs)[1], (*evs)[2]));
-    if (nfast > 0) {
-      KernelStats& sf = ctx.stats[0];
-      sf.launches += 1;
-      sf.entries += entries * (double)nfast;
-      sf.ms += ms_f;
-    }
-    if (cert_last) {
-      KernelStats& sc = ctx.stats[1];
-      sc.launches += 1;
-      sc.entries += entries;
-      sc.ms += ms_c;
+    float ms[2] = {0, 0};
+    OT_CUDA(cudaEventElapsedTime(&ms[0], (*evs)[0], (*evs)[1]));
+    OT_CUDA(cudaEventElapsedTime(&ms[1], (*evs)[1], (*evs)[2]));
+    const int64_t its[2] = {nfast, cert_last ? 1 : 0};
+    for (int kind = 0; kind < 2; ++kind) {
+      if (its[kind] <= 0) continue;
+      KernelStats& ks = ctx.stats[kind];
+      ks.launches += 1;
+      ks.entries += entries * (double)its[kind];
+      ks.ms += ms[kind];
     }
   }
   return OT_OK;
@@ -962,6 +989,32 @@ ot_status ot_debug_set_wait_limit(ot_context* ctx, uint32_t polls) {
 ot_status ot_launch_count(ot_context* ctx, int64_t* launches) {
   if (!ctx || !launches) return OT_EINVAL;
   *launches = ctx->c.launches;
+  return OT_OK;
+}
+
+ot_status ot_state_counters(ot_state* st, int64_t* out, int32_t nout) {
+  if (!st || !out || nout < 9) return OT_EINVAL;
+  Context& ctx = st->ctx->c;
+  Instance& in = st->in;
+  cudaSetDevice(ctx.device);
+  double c[40];
+  OT_CUDA(cudaMemcpyAsync(c, in.ctrl, sizeof(c), cudaMemcpyDeviceToHost, in.stream));
+  OT_CUDA(cudaStreamSynchronize(in.stream));
+  int hb[4];
+  memcpy(hb, &c[14], sizeof(hb));
+  unsigned long long rc;
+  memcpy(&rc, &c[18], sizeof(rc));
+  for (int i = 0; i < 4; ++i) out[i] = hb[i];
+  out[4] = (int64_t)rc;
+  out[5] = in.fast.nms_row;
+  out[6] = in.fast.nms_col;
+  out[7] = in.cert.nms_row;
+  out[8] = in.cert.nms_col;
+  if (nout >= 10) {
+    unsigned long long rf;
+    memcpy(&rf, &c[39], sizeof(rf));
+    out[9] = (int64_t)rf;
+  }
   return OT_OK;
 }
 

@@ -77,6 +77,7 @@ struct Instance {
   int64_t n = 0, m = 0;
   int d = 0;
   int sweep_mode = 0, cert_mode = 1;
+  double refine_on = 0.0, refine_tol = 1e-5;  // refinement of the fast sweeps' dominant terms
   bool use_graphs = true;
   // used by the batched server: stream-ordered allocation and a shared pinned read-back slot
   bool async_alloc = false;

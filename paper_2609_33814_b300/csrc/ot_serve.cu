@@ -66,7 +66,7 @@ struct Lane {
   int off[2] = {0, 0}, cnt[2] = {0, 0}, resident[2] = {0, 0};  // items per iteration of each kind
   unsigned* d_sched = nullptr;         // scheduler counters of the lane's launches
   double entries_per_sweep = 0;        // sum of n * m over the active instances
-  std::vector<cudaEvent_t> evs;        // profiling: one event between consecutive launches
+  std::vector<cudaEvent_t> evs;        // profiling: before, between and after the chunk's launches
   bool timed = false;                  // the last chunk recorded events
 };
 
@@ -110,6 +110,7 @@ int Server::lane_for(const Request* r) {
   const int mode = sweep_mode_of(r->params.precision);
   const LaunchPlan& pf = r->inst->fast;
   const LaunchPlan& pc = r->inst->cert;
+  const int cert_mode = mode == kSweepF64 ? kSweepF64 : kSweepComp;
   for (int i = 0; i < nlanes; ++i) {
     const Lane& L = lanes[i];
     if (L.d == r->prob.d && L.mode == mode && L.ce == r->params.cert_every && L.R_fast == pf.R &&
@@ -120,7 +121,7 @@ int Server::lane_for(const Request* r) {
   Lane& L = lanes[nlanes];
   L.d = r->prob.d;
   L.mode = mode;
-  L.cert_mode = mode == kSweepF64 ? kSweepF64 : kSweepComp;
+  L.cert_mode = cert_mode;
   L.ce = r->params.cert_every;
   L.R_fast = pf.R;
   L.ch_fast = pf.ch;

@@ -54,6 +54,29 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 }
 
 
+// The exponent z_pq - shift (base 2) in float-float: h = hh + hl, A = Ah + Al, the products
+// Ah_k w_k and the partial sums taken exactly by error-free transforms, then rounded once.  Its
+// error is the FP32 rounding of the (small) result, not of the 1/eps-sized terms it is made of.
+template <int D>
+__device__ __forceinline__ float comp_exponent(float hh, float hl, const float (&w)[D], const float (&Ah)[D],
+                                               const float (&Al)[D], float shift) {
+  float sb, e0;
+  two_sum(hh, -shift, sb, e0);
+  float lo = __fadd_rn(e0, hl);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    float pp, pe, s2, e2;
+    two_prod(Ah[k], w[k], pp, pe);
+    two_sum(sb, pp, s2, e2);
+    sb = s2;
+    lo = __fadd_rn(lo, __fadd_rn(e2, pe));
+    lo = __fmaf_rn(Al[k], w[k], lo);
+  }
+  return __fadd_rn(sb, lo);
+}
+
+constexpr float kNoRefine = 3.0e38f;  // refinement threshold of an item that is not refined
+
 __device__ __forceinline__ size_t pack_idx(int p, int comp) {
   return ((size_t)(p / kTQ) * kNComp + comp) * kTQ + (p % kTQ);
 }
@@ -167,6 +190,11 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
                                                          unsigned* __restrict__ sched) {
   static_assert(!(CERT && is_fast_mode(MODE)), "certificate sweeps use the compensated or FP64 mode");
   constexpr bool FAST = is_fast_mode(MODE);
+  // micro-split plan of the instance this kernel runs on (Inst::nms): the fast plan for the fast
+  // modes, the certificate plan for the compensated and FP64 sweeps (certificate iterations, and
+  // the compensated iterations before them; an instance whose every iteration runs compensated or
+  // in FP64 has the same plan in both slots)
+  constexpr int PL = FAST ? 0 : 1;
   static_assert(UPDATE || CERT, "a non-updating sweep is the standalone certificate");
   typedef typename PartT<MODE>::type Part;
   constexpr uint32_t kPackTileBytes = kNComp * kTQ * 4;  // one pack tile, all components
@@ -181,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   __shared__ int s_abort;
   __shared__ long long s_kit[2];  // per item (double-buffered by item parity): iteration k
   __shared__ int s_tk[2];         // and ticket
+  __shared__ float s_rthr[2];     // and refinement threshold (fast sweeps; kNoRefine: none)
   __shared__ int s_ring[8];  // tickets in the order the producer took them (<= kStages + 1 ahead)
 
   const int tid = threadIdx.x;
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     ps.j = ps.t / nitems;
     const Inst* Ip = insts + it.inst;
     const int qtl = it.side == 0 ? Ip->tiles_y : Ip->tiles_x;
-    const int mstp = Ip->ms_tiles[CERT ? 1 : 0][it.side];
+    const int mstp = Ip->ms_tiles[PL][it.side];
     ps.qt0 = it.ms0 * mstp;
     ps.ntl = min(qtl, (it.ms0 + it.nms) * mstp) - ps.qt0;
     ps.nst = (ps.ntl + kStageTiles - 1) / kStageTiles;
@@ -289,7 +318,27 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         }
       }
       s_tk[cseq & 1u] = t;
-      if (t < total && !s_abort) s_kit[cseq & 1u] = ld_acquire(insts[items[t % nitems].inst].k) - (UPDATE ? 0 : 1);
+      if (t < total && !s_abort) {
+        const Item& it = items[t % nitems];
+        const Inst* Ip = insts + it.inst;
+        const long long kk = ld_acquire(Ip->k) - (UPDATE ? 0 : 1);
+        s_kit[cseq & 1u] = kk;
+        // Refinement of the dominant terms (fast FP32 sweeps): the FP32 exponent's parts grow as
+        // 1/eps, so its rounding reaches e_fast = (d + 2) 2^-24 Zeps / eps (base 2; Inst::rzeps bounds
+        // the parts' magnitude times eps).  Once e_fast exceeds refine_on, chunks whose sum reaches
+        // the threshold (in units of the running shift, which the shift hints put about 2^-8 below
+        // the point's total) are re-evaluated in float-float: the unrefined rest then carries at most
+        // about refine_tol (natural log units) of error when some 16 chunks sit at the threshold.
+        float rthr = kNoRefine;
+        if constexpr (MODE == kSweepFast) {
+          if (Ip->rzeps != nullptr && Ip->refine_on > 0.0) {
+            const double inv = it.side == 0 ? row_inv_eps(Ip, kk) : 1.0 / eps_of(Ip, kk);
+            const double ef = (D + 2) * 0x1p-24 * __ldcg(Ip->rzeps) * inv;
+            if (ef > Ip->refine_on) rthr = (float)fmax(16.0 * Ip->refine_tol / ef, 0x1p-100);
+          }
+        }
+        s_rthr[cseq & 1u] = rthr;
+      }
     }
     __syncthreads();
     if (s_abort) {
@@ -304,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     const Inst* __restrict__ I = insts + item.inst;
     const int np = side == 0 ? I->n : I->m;
     const int qtiles = side == 0 ? I->tiles_y : I->tiles_x;
-    const int mst = I->ms_tiles[CERT ? 1 : 0][side];    // tiles per micro-split
+    const int mst = I->ms_tiles[PL][side];    // tiles per micro-split
     const float* __restrict__ ppack = side == 0 ? I->xpack : I->ypack;
     const int qt0 = item.ms0 * mst;
     const int qt1 = min(qtiles, (item.ms0 + item.nms) * mst);
@@ -372,6 +421,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
 #pragma unroll
         for (int k = 0; k < D; ++k) A2[r][k] = pk2(Ah[r][k], Ah[r][k]);
     }
+
 
     // running-shift floor of each point from its validated hint (fast sweeps, k >= 1)
     float hs[R];
@@ -515,6 +565,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           big |= !(t <= 0x1p64f) && (t == t);  // above 2^64 or +inf (a NaN is left to propagate)
         }
         if (__any_sync(0xffffffffu, big)) {
+          if (I->recomp != nullptr && (tid & 31) == 0) atomicAdd(I->recomp, 1ull);
 #pragma unroll
           for (int r = 0; r < R; ++r) st.acc[r] = 0ull;
 #pragma unroll 1
@@ -525,6 +576,78 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
             chunk_sums(va, cs);
 #pragma unroll
             for (int r = 0; r < R; ++r) st.acc[r] = add2(st.acc[r], cs[r]);
+          }
+        }
+        // refinement: a tile whose sum reaches rthr (for some point of the warp) is run again chunk by
+        // chunk; a chunk whose fast sum reaches rthr is replaced by its float-float evaluation
+        if constexpr (MODE == kSweepFast) {
+          const float rthr = s_rthr[cseq & 1u];
+          if (rthr < kNoRefine) {
+            bool sigt = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              float lo, hi;
+              up2(st.acc[r], lo, hi);
+              sigt |= lo + hi > rthr;
+            }
+            if (__any_sync(0xffffffffu, sigt)) {
+              // A_p in float-float, formed again here (not kept live through the fast loop)
+              float rAh[R][D], rAl[R][D];
+              {
+                const long long kk = s_kit[cseq & 1u];
+                const double sg =
+                    2.0 * I->kappa * kLog2e * (side == 0 ? row_inv_eps(I, kk) : 1.0 / eps_of(I, kk));
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                  const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+#pragma unroll
+                  for (int k = 0; k < D; ++k) {
+                    const double A = sg * (double)(p < np ? ppack[pack_idx(p, k)] : 0.0f);
+                    rAh[r][k] = __double2float_rn(A);
+                    rAl[r][k] = __double2float_rn(A - (double)rAh[r][k]);
+                  }
+                }
+              }
+#pragma unroll
+              for (int r = 0; r < R; ++r) st.acc[r] = 0ull;
+#pragma unroll 1
+              for (int c0 = 0; c0 < kTQ; c0 += CH) {
+                exponents(va, c0);
+                u64 cs[R];
+                chunk_sums(va, cs);
+                bool need[R];
+                bool any = false;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                  float lo, hi;
+                  up2(cs[r], lo, hi);
+                  need[r] = lo + hi > rthr;
+                  any |= need[r];
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                  float csr[R];
+#pragma unroll
+                  for (int r = 0; r < R; ++r) csr[r] = 0.0f;
+#pragma unroll 1
+                  for (int cc = 0; cc < CH; ++cc) {
+                    const int c = c0 + cc;
+                    float w[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) w[k] = S[k * kTQ + c];
+                    const float hh = S[D * kTQ + c], hl = S[(D + 1) * kTQ + c];
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                      csr[r] += ex2_mufu(comp_exponent<D>(hh, hl, w, rAh[r], rAl[r], st.mref[r]));
+                  }
+#pragma unroll
+                  for (int r = 0; r < R; ++r)
+                    if (need[r]) cs[r] = pk2(csr[r], 0.0f);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) st.acc[r] = add2(st.acc[r], cs[r]);
+              }
+              if ((tid & 31) == 0 && I->refined != nullptr) atomicAdd(I->refined, 1ull);
+            }
           }
         }
         // fold the tile's pair sums into the compensated running sum
@@ -694,7 +817,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     const int side = item.side;
     const Inst* __restrict__ I = insts + item.inst;
     const int np = side == 0 ? I->n : I->m;
-    const int splits = I->nms[CERT ? 1 : 0][side];  // partials per point (all micro-splits)
+    const int splits = I->nms[PL][side];  // partials per point (all micro-splits)
     const int pblks = (np + kThreads * R - 1) / (kThreads * R);
     const long long kiter = s_kit[cseq & 1u];
     const bool accn = CERT && side == 1;

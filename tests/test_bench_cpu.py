@@ -21,5 +21,7 @@ def test_reference_arm_json_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["unit"] == "entries/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    # the oracle runs in one single-threaded process per host core
+    assert d["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("serving stream")
