@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--n-points", type=int, default=1 << 16, help="ablation workload: points per cloud")
     ap.add_argument("--eta", type=float, default=0.1, help="ablation and transfer workloads: eps0")
     ap.add_argument("--budget-s", type=float, default=600.0, help="transfer workload: wall-time budget")
+    ap.add_argument("--reverse", action="store_true", help="transfer workload: the backward direction")
     ap.add_argument("--instances", type=int, default=8, help="delay workload: instance pairs")
     ap.add_argument("--delay-set", default="clouds", choices=["clouds", "grids"],
                     help="delay workload: 1024-point uniform-weight clouds (exact assignment) or 16x16 grid "
@@ -74,7 +75,9 @@ def parse():
     ap.add_argument("--precision", default="mufu", choices=["mufu", "comp", "fp64"])
     ap.add_argument("--skip", type=int, default=0, help="sweep workload: untimed iterations before the warm-up")
     ap.add_argument("--refine-on", type=float, default=0.0,
-                    help="refine_on of the fast sweeps (0: the library default, -1: off)")
+                    help="sweep workload: refine_on of the fast sweeps (0: off)")
+    ap.add_argument("--ttg-refine-on", type=float, default=2.0 ** -6,
+                    help="time-to-gap leg: refine_on of the fast sweeps (0: off)")
     ap.add_argument("--ttg-requests", type=int, default=64,
                     help="time-to-gap leg: requests of the stream solved under the stop rule with --ttg-max-iters")
     ap.add_argument("--ttg-max-iters", type=int, default=100000)
@@ -407,9 +410,11 @@ def run_config1(P, ctx, args, oracle_res):
 def run_time_to_gap(P, ctx, args, stream):
     """Time to a certified relative gap under the config's stop rule (--tol-rel, a certificate every
     --cert-every, --ttg-max-iters cap; App. G.3 best-so-far bounds): the first --ttg-requests requests
-    of the serving stream, Poisson arrivals, batched server, device-resident inputs.  Then --cmp-n of
-    its 64 x 64 requests again with the compensated exponent on every iteration, so that each of those
-    results states its FP32-exponent certified gap and iterations beside the compensated ones."""
+    of the serving stream, Poisson arrivals, batched server, device-resident inputs.  The fast sweeps
+    refine their dominant terms once the FP32 exponent's rounding bound exceeds --ttg-refine-on
+    (ot_params.refine_on).  Then --cmp-n of its 64 x 64 requests again with the compensated exponent on
+    every iteration, so that each of those results states its certified gap and iterations beside the
+    compensated ones."""
     import copy
     import torch
     a2 = copy.copy(args)
@@ -425,7 +430,7 @@ def run_time_to_gap(P, ctx, args, stream):
         if now < r.arrival_s:
             time.sleep(r.arrival_s - now)
         ids.append(srv.submit(*dv, cost_scale=probs[len(ids)].kappa, omega=probs[len(ids)].omega,
-                              zero_mass_floor=1e-15, **solve_params(a2)))
+                              zero_mass_floor=1e-15, **dict(solve_params(a2), refine_on=args.ttg_refine_on)))
     res = [srv.wait(i, -1.0)[2] for i in ids]
     makespan = time.perf_counter() - t0
     srv.close()
@@ -438,7 +443,8 @@ def run_time_to_gap(P, ctx, args, stream):
             key = f"{q.s}x{q.s} {q.cls_a}/{q.cls_b}"
             nc.setdefault(key, []).append(round(r["gap_rel"], 5))
     out = {"requests": len(reqs), "max_iters": a2.max_iters, "tol_rel": args.tol_rel, "cert_every": args.cert_every,
-           "lambda": args.serve_lam, "rate_per_s": args.rate, "makespan_s": makespan,
+           "lambda": args.serve_lam, "rate_per_s": args.rate, "refine_on": args.ttg_refine_on,
+           "makespan_s": makespan,
            "converged_frac": len(conv) / len(res),
            "time_to_gap_p50_s": float(np.percentile(ttg, 50)) if ttg else None,
            "time_to_gap_p99_s": float(np.percentile(ttg, 99)) if ttg else None,
@@ -702,14 +708,21 @@ def run_transfer(args):
     points (2^20 = 1024 x 1024 pixels) from seeded 8-component mixtures, uniform weights, kappa =
     1 / max pair cost and omega from the device, eps0 = --eta, lambda = --serve-lam, a certificate
     every --cert-every iterations, until the best relative gap reaches --tol-rel, --max-iters or
-    --budget-s of wall time (setup included)."""
+    --budget-s of wall time (setup included).  --reverse swaps source and target (the backward
+    transfer).  SM clocks are sampled during the run, and the final state's next iteration is
+    compared with the oracle on sampled rows and columns."""
     import paper_2609_33814_b300 as P
+    import oracle as O
     n = -args.size if args.size < 0 else args.size
     prob = I.rgb_problem(n, args.seed)
+    if args.reverse:
+        prob = I.Problem(prob.y, prob.x, prob.b, prob.a, prob.kappa, prob.omega, prob.name + "_reverse")
     ctx = P.Context(0)
+    clock = ClockSampler(0)
+    clock.start()
     t0 = time.perf_counter()
     S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=0.0, omega=0.0, eps0=args.eta, lam=args.serve_lam,
-                  precision="mufu", cert_every=args.cert_every)
+                  precision="mufu", cert_every=args.cert_every, refine_on=args.refine_on)
     setup_s = time.perf_counter() - t0
     curve, k, rel = [], 0, float("inf")
     while k < args.max_iters and time.perf_counter() - t0 < args.budget_s and rel > args.tol_rel:
@@ -719,17 +732,37 @@ def run_transfer(args):
         curve.append({"iter": k, "wall_s": time.perf_counter() - t0, "U_best": res["U_best"],
                       "L_best": res["L_best"], "rel_gap": rel})
     wall = time.perf_counter() - t0
+    clocks = clock.stop()
     kappa, omega = S.cost()
+    # the next iteration from the final state against the oracle, sampled rows and columns
+    lb, lbp = S.get(P.OT_LOG_BETA), S.get(P.OT_LOG_BETA_PREV)
+    lbt = lb + (lb - lbp) / args.serve_lam
+    eps = O.eps_schedule(args.eta, args.serve_lam, k)
+    S.step(1)
+    lah, lbh = S.get(P.OT_LOG_ALPHA_HAT), S.get(P.OT_LOG_BETA_HAT)
+    rng = np.random.default_rng(args.seed)
+    rows = np.sort(rng.choice(n, 8, replace=False))
+    cols = np.sort(rng.choice(n, 8, replace=False))
+    a = prob.a / prob.a.sum()
+    b = prob.b / prob.b.sum()
+    ref_r = np.log(a[rows]) - O.row_lse_sampled(rows, prob.x, prob.y, lbt, kappa, eps)
+    ref_c = np.log(b[cols]) - O.row_lse_sampled(cols, prob.y, prob.x, lah, kappa, eps)
+    scale = max(np.abs(eps * lah).max(), np.abs(eps * (lbh - np.log(b))).max())
+    err_log = max(np.abs(lah[rows] - ref_r).max(), np.abs(lbh[cols] - ref_c).max())
+    parity = {"iter": k + 1, "eps": eps, "rows": 8, "cols": 8, "max_err_log_units": float(err_log),
+              "max_err_cost_rel": float(eps * err_log / scale)}
     S.close()
     entries = 2.0 * n * n * k
     out = {"metric": "time to certified relative gap (colour transfer); implicit entries/s", "value": wall,
            "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 exp / f64 potentials, compensated certificates", "data": "synthetic",
            "config": {"workload": f"colour transfer, n = m = {n} RGB points (seeded 8-component mixtures)",
+                      "direction": "backward" if args.reverse else "forward",
                       "eps0": args.eta, "lambda": args.serve_lam, "cert_every": args.cert_every,
-                      "tol_rel": args.tol_rel, "budget_s": args.budget_s, "kappa": kappa, "omega": omega},
+                      "tol_rel": args.tol_rel, "budget_s": args.budget_s, "kappa": kappa, "omega": omega,
+                      "refine_on": args.refine_on},
            "setup_s": setup_s, "iters": k, "final_rel_gap": rel, "entries_per_s": entries / (wall - setup_s),
-           "reached_tol": rel <= args.tol_rel, "curve": curve}
+           "reached_tol": rel <= args.tol_rel, "curve": curve, "final_state_parity": parity, "clocks": clocks}
     print(json.dumps(out), flush=True)
 
 
@@ -1032,7 +1065,7 @@ def run_precision(args):
     arms = {}
     for arm in [a for a in args.study_arms.split(",") if a]:
         # arm names: comp, mufu, centred; a suffix @ON:TOL runs the arm with the fast sweeps'
-        # refinement thresholds refine_on = ON, refine_tol = TOL (mufu@-1:0: no refinement)
+        # refinement thresholds refine_on = ON, refine_tol = TOL (no suffix: no refinement)
         name, _, ref = arm.partition("@")
         centre = name == "centred"
         refine = tuple(float(v) for v in ref.split(":")) if ref else (0.0, 0.0)
@@ -1058,7 +1091,7 @@ def run_precision(args):
 def run_sweep(args):
     """One resident instance, fast iterations only: entries/s of the sweep kernels alone, after --skip
     untimed iterations (deep in the schedule the fast sweeps refine their dominant terms, see
-    ot_params; --refine-on -1 turns that off)."""
+    ot_params; --refine-on sets its threshold, 0 leaves it off)."""
     import ctypes
     import torch
     import paper_2609_33814_b300 as P

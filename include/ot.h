@@ -107,8 +107,12 @@ typedef struct {
  * With refinement, once the exponent's rounding bound e_fast (base 2) exceeds refine_on, each sweep
  * evaluates again in float-float (error-free transforms, as in the certificate sweeps) the chunks
  * of 16 points that hold a point's dominant terms, so that the terms left in FP32 carry at most
- * about refine_tol (natural log units) of error.  refine_on = 0 and refine_tol = 0 take the
- * defaults (2^-8 and 1e-5); refine_on < 0 turns refinement off. */
+ * about refine_tol (natural log units) of error.  refine_on <= 0 (the default) turns refinement
+ * off; refine_tol = 0 takes the default 1e-5.  A threshold of 2^-6 switches it on where, on grids,
+ * the FP32 rounding starts to slow the certified gap (eps ~ 6e-5 on a 128 x 128 grid).  Its cost is
+ * the float-float evaluation of every 16-point chunk that holds a dominant term of any point of a
+ * warp: about 2x per late iteration on grids, more when the points' order is not spatially coherent
+ * (a warp's points then have unrelated dominant targets). */
 typedef struct {
   double eps0;
   double lambda;
@@ -339,6 +343,41 @@ void ot_serve_destroy(ot_server* sv);
 ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, const float* x, const float* y,
                                 const double* log_r, const double* log_bt, double kappa, double eps,
                                 double* log_alpha_hat, uint64_t stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Row-sharded execution of one problem over `world` processes (one GPU each; the paper's solver runs
+ * on one GPU, this splits Algorithm 1's sweeps for problems larger than one GPU).  Every process
+ * holds the whole problem's packed operands but updates only its slice of the points of each side
+ * (contiguous runs of 512 points, ot_shard_range).  One iteration is two half-sweeps: the row
+ * update of the slice's rows over all columns, then the column update of its columns over all rows;
+ * after each half-sweep the processes exchange the packed operands their slices rewrote (an
+ * allgather of ot_shard_pack_get's bytes, applied with ot_shard_pack_put), and on certificate
+ * iterations they sum the four partial sums of Prop. 3 (an allreduce of ot_shard_cert_partials):
+ * L = sum rf + sum cg and U = sum <t, w> + omega sum delta.  The exchange is the caller's (for
+ * example torch.distributed); no kernel waits for another process.
+ *   ot_shard_range      points [*p0, *p1) of a side of np points owned by rank (no GPU needed).
+ *   ot_shard_create     the slice state of `rank` (ot_state_create's arguments and conventions);
+ *                       ot_step and ot_certificate refuse slice states, ot_state_get returns whole
+ *                       vectors of which only the slice's entries are this process's.
+ *   ot_shard_half_sweep side 0: row update of the slice, 1: column update (which completes the
+ *                       iteration); cert != 0 runs the certificate iteration's sweeps (both halves
+ *                       of one iteration must agree).
+ *   ot_shard_pack_bytes bytes of the pack slice of `side` owned by `rank` (tiles + 8 offsets).
+ *   ot_shard_pack_get   this process's pack slice of `side` into host memory.
+ *   ot_shard_pack_put   another rank's pack slice of `side` from host memory (rank 0's carries the
+ *                       pack offsets, which come from the first point).
+ *   ot_shard_cert_partials  after a certificate column half-sweep: out[0..4] = this slice's
+ *                       <r, f>, <c, g>, <t, w> (sum s_j mu_j), delta (half of sum |s_j - c_j|), and
+ *                       the certificate's eps. */
+ot_status ot_shard_range(int64_t np, int32_t rank, int32_t world, int64_t* p0, int64_t* p1);
+ot_status ot_shard_create(ot_context* ctx, const ot_problem* prob, const ot_params* params, int32_t rank,
+                          int32_t world, ot_state** out);
+ot_status ot_shard_slice(ot_state* st, int32_t side, int64_t* p0, int64_t* p1);
+ot_status ot_shard_half_sweep(ot_state* st, int32_t side, int32_t cert);
+ot_status ot_shard_pack_bytes(ot_state* st, int32_t side, int32_t rank, size_t* bytes);
+ot_status ot_shard_pack_get(ot_state* st, int32_t side, void* host_buf);
+ot_status ot_shard_pack_put(ot_state* st, int32_t side, int32_t rank, const void* host_buf);
+ot_status ot_shard_cert_partials(ot_state* st, double* out);
 
 /* Measurement support (not part of the method): kernel timing.  While enabled on a context, every
  * iteration chunk of its states records CUDA events on the launching stream around its launches

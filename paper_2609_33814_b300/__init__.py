@@ -97,6 +97,14 @@ _lib.ot_state_get.argtypes = [_P, C.c_int, _P, C.POINTER(C.c_int64)]
 _lib.ot_state_set.argtypes = [_P, C.c_int, _P, C.c_int64]
 _lib.ot_state_cost.argtypes = [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
 _lib.ot_state_counters.argtypes = [_P, C.POINTER(C.c_int64), C.c_int32]
+_lib.ot_shard_range.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+_lib.ot_shard_create.argtypes = [_P, C.POINTER(OtProblem), C.POINTER(OtParams), C.c_int32, C.c_int32, C.POINTER(_P)]
+_lib.ot_shard_slice.argtypes = [_P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+_lib.ot_shard_half_sweep.argtypes = [_P, C.c_int32, C.c_int32]
+_lib.ot_shard_pack_bytes.argtypes = [_P, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
+_lib.ot_shard_pack_get.argtypes = [_P, C.c_int32, C.c_void_p]
+_lib.ot_shard_pack_put.argtypes = [_P, C.c_int32, C.c_int32, C.c_void_p]
+_lib.ot_shard_cert_partials.argtypes = [_P, C.POINTER(C.c_double)]
 _lib.ot_set_tile_plan.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32]
 _lib.ot_get_tile_plan.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
 
@@ -328,6 +336,59 @@ class State:
         kap, om = C.c_double(), C.c_double()
         self.ctx.check(_lib.ot_state_cost(self._h, C.byref(kap), C.byref(om)), "ot_state_cost")
         return kap.value, om.value
+
+
+def shard_range(np_: int, rank: int, world: int):
+    """``ot_shard_range``: the points [p0, p1) of a side of np_ points that rank of world updates."""
+    p0, p1 = C.c_int64(), C.c_int64()
+    st = _lib.ot_shard_range(int(np_), int(rank), int(world), C.byref(p0), C.byref(p1))
+    if st != OT_OK:
+        raise OTError(st, "ot_shard_range")
+    return int(p0.value), int(p1.value)
+
+
+class ShardState(State):
+    """One slice of a row-sharded solve (``ot_shard_*``); see ``paper_2609_33814_b300.shard``."""
+
+    def __init__(self, ctx: Context, x, y, a, b, rank: int, world: int, cost_scale=0.0, omega=0.0,
+                 zero_mass_floor=0.0, **params):
+        self.ctx = ctx
+        prob, keep = make_problem(x, y, a, b, cost_scale, omega, zero_mass_floor)
+        prm = make_params(**params)
+        h = _P()
+        ctx.check(_lib.ot_shard_create(ctx.handle, C.byref(prob), C.byref(prm), int(rank), int(world), C.byref(h)),
+                  "ot_shard_create")
+        self._h = h
+        self.n, self.m, self.d = int(prob.n), int(prob.m), int(prob.d)
+        self.rank, self.world = int(rank), int(world)
+
+    def slice(self, side: int):
+        p0, p1 = C.c_int64(), C.c_int64()
+        self.ctx.check(_lib.ot_shard_slice(self._h, int(side), C.byref(p0), C.byref(p1)), "ot_shard_slice")
+        return int(p0.value), int(p1.value)
+
+    def half_sweep(self, side: int, cert: bool):
+        self.ctx.check(_lib.ot_shard_half_sweep(self._h, int(side), 1 if cert else 0), "ot_shard_half_sweep")
+
+    def pack_bytes(self, side: int, rank: int) -> int:
+        nb = C.c_size_t()
+        self.ctx.check(_lib.ot_shard_pack_bytes(self._h, int(side), int(rank), C.byref(nb)), "ot_shard_pack_bytes")
+        return int(nb.value)
+
+    def pack_get(self, side: int) -> np.ndarray:
+        buf = np.empty(self.pack_bytes(side, self.rank), np.uint8)
+        self.ctx.check(_lib.ot_shard_pack_get(self._h, int(side), buf.ctypes.data), "ot_shard_pack_get")
+        return buf
+
+    def pack_put(self, side: int, rank: int, buf: np.ndarray):
+        b = np.ascontiguousarray(buf, np.uint8)
+        assert b.size == self.pack_bytes(side, rank)
+        self.ctx.check(_lib.ot_shard_pack_put(self._h, int(side), int(rank), b.ctypes.data), "ot_shard_pack_put")
+
+    def cert_partials(self) -> np.ndarray:
+        out = (C.c_double * 5)()
+        self.ctx.check(_lib.ot_shard_cert_partials(self._h, out), "ot_shard_cert_partials")
+        return np.array(list(out))
 
 
 class Server:

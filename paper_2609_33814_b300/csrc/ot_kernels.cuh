@@ -50,6 +50,10 @@ struct Inst {
   // results do not depend on how a launch groups micro-splits into work items.
   int nms[2][2];
   int ms_tiles[2][2];
+  // Points whose updates this instance runs, per side (0 rows, 1 columns): [slice[s][0],
+  // slice[s][1]), the whole side unless the state is one slice of a row-sharded solve; the phase of
+  // a side completes when the point blocks of the slice are done.
+  int slice[2][2];
   uint32_t wait_limit;           // mbarrier polls before a sweep gives up waiting for a tile
   int alg;                       // row-update method (kAlg*): Dual (O-)BDRS or an ablation method
   double kappa, eta, lambda, omega;

@@ -132,6 +132,10 @@ extern "C" ot_status ot_row_update_noalloc(int64_t n, int64_t m, int32_t d, cons
   h.tiles_x = tiles_x;
   h.tiles_y = tiles_y;
   h.pblk_x = pblks;
+  h.slice[0][0] = 0;  // every row is updated (the column side is not swept)
+  h.slice[0][1] = (int)n;
+  h.slice[1][0] = 0;
+  h.slice[1][1] = (int)m;
   h.nms[0][0] = splits;  // fast row sweep: one micro-split per split
   h.ms_tiles[0][0] = tps;
   h.wait_limit = kWaitLimit;

@@ -256,15 +256,14 @@ int sweep_mode_of(int precision) {
 }
 
 // Refinement of the fast sweeps' dominant terms (OT_EXP_MUFU; see ot_params): on when the FP32
-// exponent's rounding bound (base 2) exceeds refine_on, with refine_tol the error the unrefined
-// terms may carry; 0 takes the default, refine_on < 0 turns it off (*on = 0 here).
-constexpr double kRefineOnDefault = 0x1p-8;
+// exponent's rounding bound (base 2) exceeds refine_on > 0, with refine_tol the error the unrefined
+// terms may carry (0: the default).  refine_on <= 0: off (*on = 0).
 constexpr double kRefineTolDefault = 1e-5;
 void refine_policy(const ot_params* q, double* on, double* tol) {
   *on = 0.0;
   *tol = q->refine_tol > 0.0 ? q->refine_tol : kRefineTolDefault;
-  if (q->precision != OT_EXP_MUFU || q->refine_on < 0.0) return;
-  *on = q->refine_on > 0.0 ? q->refine_on : kRefineOnDefault;
+  if (q->precision != OT_EXP_MUFU || !(q->refine_on > 0.0)) return;
+  *on = q->refine_on;
 }
 
 ot_status validate(Context& ctx, const ot_problem* p, const ot_params* q) {
@@ -360,6 +359,10 @@ ot_status instance_prepare(Context& ctx, Instance& in, const ot_problem* p, cons
   h.eta = q->eps0;
   h.lambda = q->lambda;
   h.alg = q->algorithm;
+  h.slice[0][0] = 0;
+  h.slice[0][1] = (int)in.n;
+  h.slice[1][0] = 0;
+  h.slice[1][1] = (int)in.m;
 
   const size_t n = in.n, m = in.m;
   size_t nsp = 0;
@@ -874,7 +877,7 @@ void ot_state_destroy(ot_state* st) {
 }
 
 ot_status ot_step(ot_state* st, int64_t n_iters, ot_result* res) {
-  if (!st || n_iters < 0) return OT_EINVAL;
+  if (!st || n_iters < 0 || st->in.shard_world > 0) return OT_EINVAL;
   cudaSetDevice(st->ctx->c.device);
   ot_status s = run_iterations(st->ctx->c, st->in, n_iters, false, false);
   if (s == OT_OK && st->in.k > 0) s = read_ctrl(st->ctx->c, st->in);
@@ -883,7 +886,7 @@ ot_status ot_step(ot_state* st, int64_t n_iters, ot_result* res) {
 }
 
 ot_status ot_certificate(ot_state* st, ot_result* res) {
-  if (!st) return OT_EINVAL;
+  if (!st || st->in.shard_world > 0) return OT_EINVAL;
   Instance& in = st->in;
   if (in.k < 1) {
     st->ctx->c.set_error("no completed iteration to certify");
@@ -1178,6 +1181,172 @@ ot_status ot_solve(ot_context* ctx, const ot_problem* prob, const ot_params* par
   fill_result(in, res);
   ot_state_destroy(st);
   return s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Row-sharded execution (one slice of the points per process; the host exchanges packed operands)
+// ---------------------------------------------------------------------------------------------
+namespace {
+constexpr int kShardUnit = 4 * kTQ;  // slice granularity in points: a multiple of every point block
+
+// Points [p0, p1) of `side` owned by `rank` of `world`: contiguous runs of whole 512-point units,
+// split as evenly as the units allow.
+void shard_range(int64_t np, int rank, int world, int64_t* p0, int64_t* p1) {
+  const int64_t units = (np + kShardUnit - 1) / kShardUnit;
+  *p0 = std::min<int64_t>(np, kShardUnit * (units * rank / world));
+  *p1 = std::min<int64_t>(np, kShardUnit * (units * (rank + 1) / world));
+}
+}  // namespace
+
+ot_status ot_shard_range(int64_t np, int32_t rank, int32_t world, int64_t* p0, int64_t* p1) {
+  if (np < 1 || world < 1 || rank < 0 || rank >= world || !p0 || !p1) return OT_EINVAL;
+  shard_range(np, rank, world, p0, p1);
+  return OT_OK;
+}
+
+ot_status ot_shard_create(ot_context* ctx, const ot_problem* prob, const ot_params* params, int32_t rank,
+                          int32_t world, ot_state** out) {
+  if (!ctx || !out || !prob || world < 1 || rank < 0 || rank >= world) return OT_EINVAL;
+  *out = nullptr;
+  const int64_t ux = (prob->n + kShardUnit - 1) / kShardUnit, uy = (prob->m + kShardUnit - 1) / kShardUnit;
+  if (prob->n < 1 || prob->m < 1 || ux < world || uy < world) {
+    ctx->c.set_error("each of the %d ranks needs at least %d points of each side", world, kShardUnit);
+    return OT_EINVAL;
+  }
+  ot_state* st = nullptr;
+  ot_status s = ot_state_create(ctx, prob, params, &st);
+  if (s != OT_OK) return s;
+  Context& c = ctx->c;
+  Instance& in = st->in;
+  in.shard_rank = rank;
+  in.shard_world = world;
+  int64_t r[2][2];
+  shard_range(in.n, rank, world, &r[0][0], &r[0][1]);
+  shard_range(in.m, rank, world, &r[1][0], &r[1][1]);
+  for (int side = 0; side < 2; ++side) {
+    in.h.slice[side][0] = (int)r[side][0];
+    in.h.slice[side][1] = (int)r[side][1];
+  }
+  // the slice's work items: the instance's items of its own point blocks, per plan and side
+  std::vector<Item> items;
+  int off[2][2];
+  const LaunchPlan* pls[2] = {&in.fast, &in.cert};
+  for (int q = 0; q < 2; ++q) {
+    const LaunchPlan& pl = *pls[q];
+    for (int side = 0; side < 2; ++side) {
+      std::vector<Item> all;
+      build_items(all, 0, side, side == 0 ? pl.pblk_row : pl.pblk_col, side == 0 ? pl.nms_row : pl.nms_col,
+                  side == 0 ? pl.group_row : pl.group_col);
+      const int rpb = kThreads * pl.R;
+      const int b0 = (int)(r[side][0] / rpb), b1 = (int)((r[side][1] + rpb - 1) / rpb);
+      off[q][side] = (int)items.size();
+      for (const Item& it : all)
+        if (it.pblk >= b0 && it.pblk < b1) items.push_back(it);
+      in.shard_nitems[q][side] = (int)items.size() - off[q][side];
+    }
+  }
+  Item* base = in.fast.d_row;  // the instance's item buffer (its items are not used by a slice)
+  for (int q = 0; q < 2; ++q)
+    for (int side = 0; side < 2; ++side) in.shard_items[q][side] = base + off[q][side];
+  cudaError_t e = cudaMemcpyAsync(base, items.data(), items.size() * sizeof(Item), cudaMemcpyHostToDevice, in.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(in.d_inst, &in.h, sizeof(Inst), cudaMemcpyHostToDevice, in.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(in.stream);
+  if (e != cudaSuccess) {
+    c.set_error("shard set-up failed: %s", cudaGetErrorString(e));
+    ot_state_destroy(st);
+    return OT_ECUDA;
+  }
+  *out = st;
+  return OT_OK;
+}
+
+ot_status ot_shard_slice(ot_state* st, int32_t side, int64_t* p0, int64_t* p1) {
+  if (!st || side < 0 || side > 1 || st->in.shard_world < 1) return OT_EINVAL;
+  if (p0) *p0 = st->in.h.slice[side][0];
+  if (p1) *p1 = st->in.h.slice[side][1];
+  return OT_OK;
+}
+
+ot_status ot_shard_half_sweep(ot_state* st, int32_t side, int32_t cert) {
+  if (!st || side < 0 || side > 1 || st->in.shard_world < 1) return OT_EINVAL;
+  Context& ctx = st->ctx->c;
+  Instance& in = st->in;
+  cudaSetDevice(ctx.device);
+  const int q = cert ? 1 : 0;
+  const LaunchPlan& pl = cert ? in.cert : in.fast;
+  SweepFn fn = get_sweep(in.d, pl.mode, pl.R, pl.ch, cert ? 1 : 0);
+  const int nitems = in.shard_nitems[q][side];
+  OT_CUDA(launch_sweep(fn, in.d_inst, in.shard_items[q][side], nitems, 1, std::min(nitems, pl.resident), in.sched,
+                       in.stream));
+  ctx.launches += 1;
+  if (side == 1) {
+    in.k += 1;
+    if (cert) in.last_cert_k = in.k;
+  }
+  return read_ctrl(ctx, in);
+}
+
+// A pack slice travels as its tiles (kNComp x kTQ floats each) followed by the eight pack offsets,
+// which every rank takes from rank 0 (they come from the first point, which rank 0 owns).
+ot_status ot_shard_pack_bytes(ot_state* st, int32_t side, int32_t rank, size_t* bytes) {
+  if (!st || !bytes || side < 0 || side > 1 || st->in.shard_world < 1 || rank < 0 || rank >= st->in.shard_world)
+    return OT_EINVAL;
+  int64_t p0, p1;
+  shard_range(side == 0 ? st->in.n : st->in.m, rank, st->in.shard_world, &p0, &p1);
+  const int64_t tiles = (p1 + kTQ - 1) / kTQ - p0 / kTQ;
+  *bytes = (size_t)tiles * kNComp * kTQ * sizeof(float) + 8 * sizeof(double);
+  return OT_OK;
+}
+
+static ot_status shard_pack_copy(ot_state* st, int32_t side, int32_t rank, void* host, bool to_host) {
+  Context& ctx = st->ctx->c;
+  Instance& in = st->in;
+  cudaSetDevice(ctx.device);
+  int64_t p0, p1;
+  shard_range(side == 0 ? in.n : in.m, rank, in.shard_world, &p0, &p1);
+  const int64_t t0 = p0 / kTQ, t1 = (p1 + kTQ - 1) / kTQ;
+  const size_t tile_bytes = (size_t)kNComp * kTQ * sizeof(float);
+  float* pack = side == 0 ? in.h.xpack : in.h.ypack;
+  char* dev = (char*)(pack + (size_t)t0 * kNComp * kTQ);
+  char* h = (char*)host;
+  const size_t nb = (size_t)(t1 - t0) * tile_bytes;
+  double* goff = in.ctrl + 24;
+  if (to_host) {
+    OT_CUDA(cudaMemcpyAsync(h, dev, nb, cudaMemcpyDeviceToHost, in.stream));
+    OT_CUDA(cudaMemcpyAsync(h + nb, goff, 8 * sizeof(double), cudaMemcpyDeviceToHost, in.stream));
+  } else {
+    OT_CUDA(cudaMemcpyAsync(dev, h, nb, cudaMemcpyHostToDevice, in.stream));
+    if (rank == 0) OT_CUDA(cudaMemcpyAsync(goff, h + nb, 8 * sizeof(double), cudaMemcpyHostToDevice, in.stream));
+  }
+  OT_CUDA(cudaStreamSynchronize(in.stream));
+  return OT_OK;
+}
+
+ot_status ot_shard_pack_get(ot_state* st, int32_t side, void* host_buf) {
+  if (!st || !host_buf || side < 0 || side > 1 || st->in.shard_world < 1) return OT_EINVAL;
+  return shard_pack_copy(st, side, st->in.shard_rank, host_buf, true);
+}
+
+ot_status ot_shard_pack_put(ot_state* st, int32_t side, int32_t rank, const void* host_buf) {
+  if (!st || !host_buf || side < 0 || side > 1 || st->in.shard_world < 1 || rank < 0 ||
+      rank >= st->in.shard_world || rank == st->in.shard_rank)
+    return OT_EINVAL;
+  return shard_pack_copy(st, side, rank, const_cast<void*>(host_buf), false);
+}
+
+ot_status ot_shard_cert_partials(ot_state* st, double* out) {
+  if (!st || !out || st->in.shard_world < 1) return OT_EINVAL;
+  if (st->in.last_cert_k != st->in.k) {
+    st->ctx->c.set_error("the last column half-sweep was not a certificate sweep");
+    return OT_EINVAL;
+  }
+  const double* c = st->in.h_ctrl;  // read back by the half-sweep
+  out[0] = c[kCertRF];
+  out[1] = c[kCertCG];
+  out[2] = c[kCertCostZ];
+  out[3] = c[kCertDelta];
+  out[4] = c[kCertEps];
+  return OT_OK;
 }
 
 }  // extern "C"

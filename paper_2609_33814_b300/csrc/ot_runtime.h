@@ -93,6 +93,11 @@ struct Instance {
   double elapsed_s = 0, elapsed_base = 0;
   int stop = OT_STOP_NONE;
   int device_errors = 0;
+  // Row-sharded execution (ot_shard_*): this process's rank of `shard_world`, and the work items of
+  // its slice per plan (0 fast, 1 certificate) and side, written over the instance's item buffer.
+  int shard_rank = -1, shard_world = 0;
+  Item* shard_items[2][2] = {};
+  int shard_nitems[2][2] = {};
   std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
   std::map<std::pair<int64_t, int>, std::vector<cudaEvent_t>> graph_events;  // profiling mode
 };

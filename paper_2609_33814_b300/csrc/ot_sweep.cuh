@@ -819,6 +819,10 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     const int np = side == 0 ? I->n : I->m;
     const int splits = I->nms[PL][side];  // partials per point (all micro-splits)
     const int pblks = (np + kThreads * R - 1) / (kThreads * R);
+    // point blocks this instance updates on this side: all of them, or the slice of a sharded state
+    // (Inst::slice: point ranges aligned to 512 points, so to every R)
+    const int own_blks = (min(I->slice[side][1], np) + kThreads * R - 1) / (kThreads * R) -
+                         I->slice[side][0] / (kThreads * R);
     const long long kiter = s_kit[cseq & 1u];
     const bool accn = CERT && side == 1;
     const Part* part = reinterpret_cast<const Part*>(I->part);
@@ -1001,7 +1005,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     fence_proxy_async_global();  // the packed h just written is read by bulk copies of a later phase
     __threadfence();
     __syncthreads();
-    if (tid == 0) s_flag = (atomicAdd(I->done, 1u) == (unsigned)(pblks - 1));
+    if (tid == 0) s_flag = (atomicAdd(I->done, 1u) == (unsigned)(own_blks - 1));
     __syncthreads();
     if (!s_flag) continue;
     __threadfence();

@@ -22,9 +22,10 @@ Each error is stated twice:
   pack offset) is at most Z = max|h - G| + sum_k max|A_k| max|w_k| in magnitude and takes at most
   d + 2 roundings of 2^-24 relative, and the log-sum-exp is 1-Lipschitz in its terms; the offset the
   GPU used is up to two iterations older than the one formed here, so Z is doubled:
-  bound = ln 2 (2 (d + 2) 2^-24 Z + 2^-16).  Refined sweeps (the default once that rounding
-  exceeds refine_on): the dominant terms are formed in float-float and rounded once at their own
-  small size, and the terms left in FP32 carry about refine_tol, so bound = 8 refine_tol + 2^-16.
+  bound = ln 2 (2 (d + 2) 2^-24 Z + 2^-16).  Refined sweeps (refine_on = 2^-8, which switches the
+  refinement on at these states): the dominant terms are formed in float-float and rounded once at
+  their own small size, and the terms left in FP32 carry about refine_tol, so
+  bound = 8 refine_tol + 2^-16.
 """
 import numpy as np
 import pytest
@@ -117,7 +118,7 @@ def test_grid128_deep_in_the_schedule(ctx, lam, checkpoints, refine):
     with the fast sweeps in plain FP32 and refined (their dominant terms in float-float)."""
     prob = I.grid_problem(128, 2609, "gaussmix", "cauchy")
     S = ctx.state(prob.x, prob.y, prob.a, prob.b, cost_scale=prob.kappa, omega=prob.omega, eps0=1.0, lam=lam,
-                  precision="mufu", cert_every=0, zero_mass_floor=1e-15, refine_on=0.0 if refine else -1.0)
+                  precision="mufu", cert_every=0, zero_mass_floor=1e-15, refine_on=2.0 ** -8 if refine else 0.0)
     rng = np.random.default_rng(7)
     done = 0
     for kc in checkpoints:
