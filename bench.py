@@ -541,10 +541,23 @@ def run_ours(args, rank: int, world: int):
     lib.ot_profile_enable(ctx.handle, 0)
     clocks = clock.stop()
     kst = []
+    launch_breakdown = None
     if srv is not None:
         srv.profile(False)
         nl = ctypes.c_int64(srv.stats()["launches"])
         kst = [srv.kernel_stats(kind) for kind in range(2)]
+        log = srv.launch_log()
+        if len(log):
+            # fast launches grouped by the number of instances in the lane: share of the kernel time,
+            # and entries/s within the group
+            launch_breakdown = []
+            for lo, hi in ((1, 1), (2, 4), (5, 16), (17, 64), (65, 1 << 30)):
+                m = (log[:, 2] >= lo) & (log[:, 2] <= hi)
+                if m.any():
+                    launch_breakdown.append({"instances": f"{lo}-{hi}" if hi < (1 << 30) else f">={lo}",
+                                             "launches": int(m.sum()),
+                                             "time_share": float(log[m, 1].sum() / log[:, 1].sum()),
+                                             "entries_per_s": float(log[m, 0].sum() / (log[m, 1].sum() / 1e3))})
     else:
         nl = ctypes.c_int64()
         lib.ot_launch_count(ctx.handle, ctypes.byref(nl))
@@ -627,6 +640,7 @@ def run_ours(args, rank: int, world: int):
         "time_to_gap_converged_median_s": (float(np.median(results[-1]["ttg_conv"]))
                                            if results[-1]["ttg_conv"] else None),
         "serial_baseline": serial,
+        "launch_breakdown": launch_breakdown,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "entries/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "traffic_basis": "bytes per launch: 0.036 B/entry from an ncu capture of one serving chunk, "

@@ -310,6 +310,10 @@ ot_status ot_serve_reset_stats(ot_server* sv);
  * summed over the instances a launch covers). */
 ot_status ot_serve_profile_enable(ot_server* sv, int on);
 ot_status ot_serve_profile_read(ot_server* sv, int kind, int64_t* launches, double* entries, double* ms);
+/* The same per fast launch, in launch order: out[3 i .. 3 i + 2] = (implicit entries, milliseconds,
+ * instances in the lane) for i < min(*count, max_launches); *count receives the number recorded since
+ * the last reset.  out may be NULL (count only). */
+ot_status ot_serve_profile_launches(ot_server* sv, double* out, int64_t max_launches, int64_t* count);
 void ot_serve_destroy(ot_server* sv);
 
 /* ---------------------------------------------------------------------------------------------

@@ -128,6 +128,7 @@ _lib.ot_serve_destroy.argtypes = [_P]
 _lib.ot_serve_profile_enable.argtypes = [_P, C.c_int]
 _lib.ot_serve_profile_read.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                        C.POINTER(C.c_double)]
+_lib.ot_serve_profile_launches.argtypes = [_P, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
 _lib.ot_profile_enable.argtypes = [_P, C.c_int]
 _lib.ot_profile_reset.argtypes = [_P]
 _lib.ot_profile_read.argtypes = [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -455,6 +456,15 @@ class Server:
         n, e, ms = C.c_int64(), C.c_double(), C.c_double()
         _lib.ot_serve_profile_read(self._h, int(kind), C.byref(n), C.byref(e), C.byref(ms))
         return n.value, e.value, ms.value
+
+    def launch_log(self) -> np.ndarray:
+        """Per fast launch since the last reset: rows (implicit entries, ms, instances in the lane)."""
+        n = C.c_int64()
+        _lib.ot_serve_profile_launches(self._h, None, 0, C.byref(n))
+        out = np.zeros((n.value, 3), np.float64)
+        if n.value:
+            _lib.ot_serve_profile_launches(self._h, out.ctypes.data, n.value, C.byref(n))
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

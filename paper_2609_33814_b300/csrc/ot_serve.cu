@@ -92,6 +92,8 @@ struct Server {
   int64_t submitted = 0, completed = 0, cancelled = 0, failed = 0, chunks = 0;
   double entries = 0, t_stats = 0;
   std::string fatal;
+  // profiling: per fast launch (entries, milliseconds, instances in the lane), in launch order
+  std::vector<double> launch_log;
   bool profile = false;
 
   void loop();
@@ -424,6 +426,12 @@ void Server::loop() {
         ks.launches += 1;
         ks.entries += 2.0 * L.entries_per_sweep * iters[kind];  // row and column sweeps
         ks.ms += ms;
+        if (kind == 0) {
+          std::lock_guard<std::mutex> lk(mu);
+          launch_log.push_back(2.0 * L.entries_per_sweep * iters[kind]);
+          launch_log.push_back(ms);
+          launch_log.push_back((double)L.active.size());
+        }
       }
     }
     std::vector<Request*> done_now;
@@ -707,11 +715,23 @@ ot_status ot_serve_profile_read(ot_server* sv, int kind, int64_t* launches, doub
   return OT_OK;
 }
 
+ot_status ot_serve_profile_launches(ot_server* sv, double* out, int64_t max_launches, int64_t* count) {
+  if (!sv || !count) return OT_EINVAL;
+  Server& S = sv->s;
+  std::lock_guard<std::mutex> lk(S.mu);
+  const int64_t n = (int64_t)S.launch_log.size() / 3;
+  *count = n;
+  if (out)
+    for (int64_t i = 0; i < std::min(n, max_launches) * 3; ++i) out[i] = S.launch_log[i];
+  return OT_OK;
+}
+
 ot_status ot_serve_reset_stats(ot_server* sv) {
   if (!sv) return OT_EINVAL;
   Server& S = sv->s;
   std::lock_guard<std::mutex> lk(S.mu);
   S.latencies.clear();
+  S.launch_log.clear();
   for (auto& k : S.ctx.stats) k = KernelStats();
   S.ctx.launches = 0;
   S.completed = S.cancelled = S.failed = S.chunks = 0;
