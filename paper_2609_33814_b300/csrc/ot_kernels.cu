@@ -34,6 +34,25 @@ __global__ void pack_coords_kernel(const float* __restrict__ pts, int npts, int 
   if (p < npts) n2[p] = kappa * s;
 }
 
+// Coordinate runs of a 2-D pack (read by the fast sweeps, kRunCols): for each tile, 1 + k in the
+// first entry of its free component (kNComp - 1) when coordinate k takes one value over every
+// aligned group of kRunCols points of the tile, else 0 (coordinate 1 preferred).  Padding points are
+// left out: their h = kPadH makes each of their terms vanish whatever coordinate is used.  One
+// block of kTQ threads per tile; runs after pack_coords_kernel (and its centring) on the same stream.
+__global__ void tile_runs_kernel(float* __restrict__ pack, int npts) {
+  const int t = blockIdx.x, c = threadIdx.x;
+  const int p = t * kTQ + c;
+  const int head = t * kTQ + (c & ~(kRunCols - 1));  // a valid point whenever p is
+  bool same0 = true, same1 = true;
+  if (p < npts) {
+    same0 = pack[pack_idx(p, 0)] == pack[pack_idx(head, 0)];
+    same1 = pack[pack_idx(p, 1)] == pack[pack_idx(head, 1)];
+  }
+  const int all0 = __syncthreads_and(same0 ? 1 : 0);
+  const int all1 = __syncthreads_and(same1 ? 1 : 0);
+  if (c == 0) pack[pack_idx(t * kTQ, kNComp - 1)] = all1 ? 2.0f : (all0 ? 1.0f : 0.0f);
+}
+
 // Exact centring of the two clouds (translation leaves the squared-Euclidean cost unchanged).  The
 // FP32 exponent of the fast sweeps rounds at the scale of kappa ||w||^2 / eps and of <A_p, w_q>, so
 // coordinates near the origin make it more accurate; the translation is only applied when it is
@@ -259,7 +278,11 @@ cudaError_t launch_pack_coords(const float* pts, int npts, int d, int tiles, dou
   const int tot = tiles * kTQ;
   void* args[] = {(void*)&pts, (void*)&npts, (void*)&d, (void*)&tiles, (void*)&kappa, (void*)&pack, (void*)&n2,
                   (void*)&origin};
-  return cudaLaunchKernel((const void*)pack_coords_kernel, dim3((tot + 255) / 256), dim3(256), args, 0, s);
+  cudaError_t e = cudaLaunchKernel((const void*)pack_coords_kernel, dim3((tot + 255) / 256), dim3(256), args, 0, s);
+  if (e != cudaSuccess || d != 2 || tiles <= 0) return e;
+  static_assert(kNComp - 1 >= 2 + 2, "a 2-D pack has a free component for the run flags");
+  void* a2[] = {(void*)&pack, (void*)&npts};
+  return cudaLaunchKernel((const void*)tile_runs_kernel, dim3(tiles), dim3(kTQ), a2, 0, s);
 }
 
 // The centring translation of the two clouds into origin (3 floats): zeros unless it is exact;

@@ -42,6 +42,22 @@ constexpr float kHintMargin = 8.0f;
 constexpr float kHintTol = 16.0f;
 constexpr float kHintGuard = 72.0f;
 constexpr float kPadH = -1.0e30f;        // h of padding points: contributes exp2(-1e30) = 0
+// Coordinate runs of 2-D packs (see tile_runs_kernel): a tile's free pack component (kNComp - 1)
+// holds, in its first entry, 1 + k when coordinate k is constant within every aligned group of
+// kRunCols points of the tile, else 0.
+constexpr int kRunCols = 16;
+// The fast sweeps' chunk loop is unrolled twice (the exp2 and sums of one chunk overlap the next
+// chunk's exponents) and the first chunk of a micro-split, which sets the running shifts, runs
+// outside it.  Measured on B300 against no unrolling and no peeling: +1.5 % (256^2, 512^2 grids),
+// +10 % (2^18 RGB points).
+#ifndef OT_CHUNK_UNROLL
+#define OT_CHUNK_UNROLL 2
+#endif
+#ifndef OT_PEEL_FRESH
+#define OT_PEEL_FRESH 1
+#endif
+constexpr int kChunkUnroll = OT_CHUNK_UNROLL;
+constexpr bool kPeelFresh = OT_PEEL_FRESH != 0;
 
 // ---------------------------------------------------------------------------------------------
 // Small helpers
@@ -449,10 +465,42 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       const float* __restrict__ S = smem + stg * kStageFloats + tt * (kNComp * kTQ);
 
       if constexpr (FAST) {
+        // The tile body is instantiated per coordinate-run variant KC (2-D packs only, Inst::runs
+        // below): -1 general; 0 or 1 when coordinate KC is the same for every point of each aligned
+        // group of kRunCols tile points (a row-major pixel grid's row coordinate), so that chunk's
+        // exponents share the term A_p,KC w_KC - shift_p and cost one f32x2 FMA and one add per pair.
+        auto fast_tile = [&](auto kc_tag) {
+        constexpr int KC = decltype(kc_tag)::value;
+        static_assert(KC < 0 || (D == 2 && kRunCols % CH == 0), "coordinate runs: 2-D packs, chunks within a run");
         // Per chunk of CH columns: exponents (f32x2 FMAs), chunk maximum and lazy rescale, then
         // exp2 on the SFU with a pairwise sum.
         u64 va[R][CH / 2];
         auto exponents = [&](u64 (&v)[R][CH / 2], int c0) {
+          if constexpr (KC >= 0) {
+            constexpr int KV = 1 - KC;
+            const float wc = S[KC * kTQ + c0];  // the chunk's shared coordinate
+            u64 T2[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              float ac, ac1;
+              up2(A2[r][KC], ac, ac1);
+              const float t = __fmaf_rn(ac, wc, -st.mref[r]);
+              T2[r] = pk2(t, t);
+            }
+#pragma unroll
+            for (int gq = 0; gq < CH / 4; ++gq) {
+              const int c = c0 + 4 * gq;
+              const float4 hq = *reinterpret_cast<const float4*>(S + D * kTQ + c);
+              const float4 wq = *reinterpret_cast<const float4*>(S + KV * kTQ + c);
+              const u64 h01 = pk2(hq.x, hq.y), h23 = pk2(hq.z, hq.w);
+              const u64 w01 = pk2(wq.x, wq.y), w23 = pk2(wq.z, wq.w);
+#pragma unroll
+              for (int r = 0; r < R; ++r) {
+                v[r][2 * gq] = add2(fma2(A2[r][KV], w01, h01), T2[r]);
+                v[r][2 * gq + 1] = add2(fma2(A2[r][KV], w23, h23), T2[r]);
+              }
+            }
+          } else {
 #pragma unroll
           for (int gq = 0; gq < CH / 4; ++gq) {
             const int c = c0 + 4 * gq;
@@ -477,6 +525,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
               v[r][2 * gq] = sub2(a0, st.M2[r]);
               v[r][2 * gq + 1] = sub2(a1, st.M2[r]);
             }
+          }
           }
         };
         // chunk maximum (max3 tree), one warp vote, rare lazy rescale of shift and sums
@@ -547,10 +596,20 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         // first chunk of a work item takes the exact maximum to set the shift.  If the tile's sum
         // then exceeds 2^64 (or overflowed), the tile, still in shared memory, is recomputed chunk
         // by chunk with the exact maximum and an exact power-of-two rescale of the running sums.
-#pragma unroll 1
-        for (int c0 = 0; c0 < kTQ; c0 += CH) {
+        int c0s = 0;
+        if (kPeelFresh && fresh) {  // the first chunk of a micro-split sets the running shifts
+          exponents(va, 0);
+          rescale(va);
+          u64 cs[R];
+          chunk_sums(va, cs);
+#pragma unroll
+          for (int r = 0; r < R; ++r) st.acc[r] = add2(st.acc[r], cs[r]);
+          c0s = CH;
+        }
+#pragma unroll kChunkUnroll
+        for (int c0 = c0s; c0 < kTQ; c0 += CH) {
           exponents(va, c0);
-          if (fresh) rescale(va);
+          if (!kPeelFresh && fresh) rescale(va);
           u64 cs[R];
           chunk_sums(va, cs);
 #pragma unroll
@@ -657,6 +716,15 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           up2(st.acc[r], lo, hi);
           st.acc[r] = 0ull;
           kahan_add(st.s[r], st.kc[r], lo + hi);
+        }
+        };  // fast_tile
+        if constexpr (D == 2) {
+          const float runs = S[(kNComp - 1) * kTQ];
+          if (runs == 2.0f) fast_tile(std::integral_constant<int, 1>{});
+          else if (runs == 1.0f) fast_tile(std::integral_constant<int, 0>{});
+          else fast_tile(std::integral_constant<int, -1>{});
+        } else {
+          fast_tile(std::integral_constant<int, -1>{});
         }
       } else {
         // compensated (float-float) or FP64 exponent

@@ -51,7 +51,30 @@ def _problem(kind, seed):
         x = I.random_cloud(5, 2, seed)
         y = I.random_cloud(1, 2, seed + 1)
         return I.Problem(x, y, I.uniform_weights(5, seed + 2), np.ones(1), 0.5, 1.0, "one_col")
+    # 2-D packs whose tiles share a coordinate along aligned runs of points take the fast sweeps'
+    # run variant; these cases cover the other coordinate, no runs, and runs on one side only
+    if kind == "grid16_cm":  # column-major grid: the first coordinate is constant along each run
+        p = I.grid_problem(16, seed)
+        return I.Problem(np.ascontiguousarray(p.x[:, ::-1]), np.ascontiguousarray(p.y[:, ::-1]), p.a, p.b,
+                         p.kappa, p.omega, kind)
+    if kind == "grid48":
+        return I.grid_problem(48, seed, "gaussmix", "uniform")
+    if kind == "grid20_perm":  # a grid in random order: no runs
+        p = I.grid_problem(20, seed)
+        rng = np.random.default_rng(seed)
+        px, py = rng.permutation(400), rng.permutation(400)
+        return I.Problem(p.x[px], p.y[py], p.a[px], p.b[py], p.kappa, p.omega, kind)
+    if kind == "grid_mixed":  # 24 x 24 sources (runs of 24 straddle the aligned groups), 16 x 17 targets
+        x, y = _grid_xy(24, 24), _grid_xy(16, 17)
+        kappa = 1.0 / float(((x[:, None, :] - y[None, :, :]) ** 2).sum(-1).max())
+        return I.Problem(x, y, I.uniform_weights(576, seed), I.uniform_weights(272, seed + 1), kappa, 1.0, kind)
     raise ValueError(kind)
+
+
+def _grid_xy(sx, sy):
+    """Integer coordinates of an sx-by-sy pixel grid, row-major (the first coordinate varies fastest)."""
+    iy, ix = np.meshgrid(np.arange(sy), np.arange(sx), indexing="ij")
+    return np.stack([ix.ravel(), iy.ravel()], axis=1).astype(np.float32)
 
 
 def _potential_err(st_o, lah, lbh, eps, logc):
@@ -75,7 +98,8 @@ def _gpu_state(ctx, prob, eta, lam, precision, cert_every, st_o=None):
 
 CASES = [("grid16", 1.0, 0), ("grid16", 1.0, 7), ("grid32", 1.0, 3), ("grid16_gauss", 1.5, 5),
          ("grid16_sparse", 1.99, 4), ("ragged3", 1.5, 3), ("line", 1.0, 6), ("one_row", 1.2, 2),
-         ("one_col", 1.0, 2)]
+         ("one_col", 1.0, 2), ("grid16_cm", 1.0, 5), ("grid48", 1.3, 4), ("grid20_perm", 1.0, 3),
+         ("grid_mixed", 1.5, 6)]
 
 
 @pytest.mark.parametrize("precision", ["mufu", "poly", "split", "comp", "fp64"])
