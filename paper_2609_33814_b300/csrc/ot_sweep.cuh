@@ -141,12 +141,25 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
+// Split partial per point: (shift, sum) in the fast sweeps, (shift, sum, cost-weighted sum, 0) in the
+// compensated ones, PartF64 in the FP64 ones.
 template <int MODE>
-struct PartT { typedef float4 type; };
+struct PartT { typedef float2 type; };
+template <>
+struct PartT<kSweepComp> { typedef float4 type; };
 template <>
 struct PartT<kSweepF64> { typedef PartF64 type; };
+// Row stride (points) of the partials of one micro-split: a multiple of 4 in the fast sweeps, so
+// that a pair of adjacent points' (shift, sum) partials is one aligned 16-byte load.
+template <int MODE>
+__host__ __device__ constexpr size_t part_stride(int np) {
+  return is_fast_mode(MODE) ? (size_t)((np + 3) & ~3) : (size_t)np;
+}
+__device__ __forceinline__ float part_z(const float2&) { return 0.0f; }
+__device__ __forceinline__ float part_z(const float4& v) { return v.z; }
 
 // Partials written by other CTAs are read through L2 (the L1 of this SM is not coherent).
+__device__ __forceinline__ float2 load_part(const float2* p) { return __ldcg(p); }
 __device__ __forceinline__ float4 load_part(const float4* p) { return __ldcg(p); }
 __device__ __forceinline__ PartF64 load_part(const PartF64* p) {
   const double2* q = reinterpret_cast<const double2*>(p);
@@ -227,6 +240,9 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   __shared__ int s_tk[2];         // and ticket
   __shared__ float s_rthr[2];     // and refinement threshold (fast sweeps; kNoRefine: none)
   __shared__ int s_ring[8];  // tickets in the order the producer took them (<= kStages + 1 ahead)
+  __shared__ double s_ep[9];  // epilogue scalars of the current item (formed by thread 0)
+  __shared__ int s_use_hint;
+  __shared__ long long s_ring_k[8];  // per ring slot: the iteration its item's dependency check saw
 
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -239,10 +255,11 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   const int total = nitems * iters;
   // has the instance finished the phase that ticket (item it, launch iteration j) depends on?
   // (k0 does not change while the instance still has items in this launch)
-  auto dep_met = [&](const Item& it, int j) -> bool {
+  // Once met, the item's iteration is k0 + j: the instance's k cannot pass it before the item is done.
+  auto dep_met = [&](const Item& it, int j, long long& need) -> bool {
     if constexpr (!UPDATE) return true;  // the standalone certificate reads a finished state
     const Inst* Ip = insts + it.inst;
-    const long long need = __ldcg(Ip->k0) + j;
+    need = __ldcg(Ip->k0) + j;
     return it.side == 0 ? ld_acquire(Ip->k) >= need : ld_acquire(Ip->rows) >= need + 1;
   };
 
@@ -282,8 +299,10 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
   auto pr_ready = [&]() -> bool {
     if (ps.t >= total) return false;
     if (!ps.ok) {
-      if (!dep_met(ps.item, ps.j)) return false;
+      long long need = 0;
+      if (!dep_met(ps.item, ps.j, need)) return false;
       fence_proxy_async_global();
+      s_ring_k[ps.seq & 7u] = need;
       ps.ok = true;
     }
     return true;
@@ -318,7 +337,8 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       if (ps.seq == cseq && t < total && !ps.ok) {
         const Inst* Ip = insts + ps.item.inst;
         uint32_t polls = 0;
-        while (!dep_met(ps.item, ps.j)) {
+        long long need = 0;
+        while (!dep_met(ps.item, ps.j, need)) {
           if (polls++ >= Ip->wait_limit || *(volatile unsigned*)&sched[2] != 0u) {
             atomicOr(Ip->err, kErrTimeout);
             atomicExch(&sched[2], 1u);
@@ -329,6 +349,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         }
         if (!s_abort) {
           fence_proxy_async_global();
+          s_ring_k[ps.seq & 7u] = need;
           ps.ok = true;
           refill(gcons);
         }
@@ -337,7 +358,9 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       if (t < total && !s_abort) {
         const Item& it = items[t % nitems];
         const Inst* Ip = insts + it.inst;
-        const long long kk = ld_acquire(Ip->k) - (UPDATE ? 0 : 1);
+        // an updating item's iteration was seen by its dependency check; the standalone certificate
+        // certifies the last completed iteration
+        const long long kk = UPDATE ? s_ring_k[cseq & 7u] : ld_acquire(Ip->k) - 1;
         s_kit[cseq & 1u] = kk;
         // Refinement of the dominant terms (fast FP32 sweeps): the FP32 exponent's parts grow as
         // 1/eps, so its rounding reaches e_fast = (d + 2) 2^-24 Zeps / eps (base 2; Inst::rzeps bounds
@@ -424,9 +447,11 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           Part pr;
           pr.x = st.mref[r];
           pr.y = st.s[r];
-          pr.z = st.n[r];
-          pr.w = 0;
-          part[(size_t)ms * np + p] = pr;
+          if constexpr (!FAST) {
+            pr.z = st.n[r];
+            pr.w = 0;
+          }
+          part[(size_t)ms * part_stride<MODE>(np) + p] = pr;
         }
       }
     };
@@ -443,11 +468,19 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     float hs[R];
     bool use_hint = false;
     if constexpr (FAST) {
-      use_hint = kiter >= 1 && I->hint_bad != nullptr && __ldcg(&I->hint_bad[2 * side + ((kiter - 1) & 1)]) == 0;
+      // the hints are loaded with the miss counter (one round trip), and used if it is zero
+      const bool have = kiter >= 1 && I->hint_bad != nullptr && I->hint[side] != nullptr;
+      float hv[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
-        hs[r] = (use_hint && p < np) ? floorf(__ldcg(&I->hint[side][p])) - kHintMargin : -INFINITY;
+        hv[r] = (have && p < np) ? __ldcg(&I->hint[side][p]) : 0.0f;
+      }
+      use_hint = have && __ldcg(&I->hint_bad[2 * side + ((kiter - 1) & 1)]) == 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+        hs[r] = (use_hint && p < np) ? floorf(hv[r]) - kHintMargin : -INFINITY;
       }
     }
 
@@ -896,34 +929,177 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     const Part* part = reinterpret_cast<const Part*>(I->part);
     __threadfence();
     __syncthreads();
-    if (tid == 0)
-      s_flag = (atomicAdd(&I->cnt[item.pblk], (unsigned)item.nms) + (unsigned)item.nms == (unsigned)splits);
+    if (tid == 0) {
+      const bool last =
+          atomicAdd(&I->cnt[item.pblk], (unsigned)item.nms) + (unsigned)item.nms == (unsigned)splits;
+      s_flag = last;
+      if (last) {
+        __threadfence();
+        // The epilogue's scalars, formed once for the CTA (FP64 divisions are slow on this GPU):
+        // eps_k, 1 / eps_k, 1 / lambda, the next row sweep's inverse temperature (for the column
+        // pack) and this one's, the hint ratio (hints predict this side's next log-sum-exp: this
+        // one scaled by the ratio of the temperatures), the offsets of the pack this sweep read
+        // (the other side's) for this and the next iteration and of the pack this epilogue writes.
+        const double e = eps_of(I, kiter);
+        const double ir = row_inv_eps(I, kiter);
+        s_ep[0] = e;
+        s_ep[1] = 1.0 / e;
+        s_ep[2] = 1.0 / I->lambda;
+        s_ep[3] = row_inv_eps(I, kiter + 1);
+        s_ep[4] = ir;
+        s_ep[5] = side == 0 ? row_inv_eps(I, kiter + 1) / ir : e / eps_of(I, kiter + 1);
+        s_ep[6] = pack_offset(I, 1 - side, kiter);
+        s_ep[7] = pack_offset(I, 1 - side, kiter + 1);
+        s_ep[8] = side == 0 ? pack_offset(I, 0, kiter) : pack_offset(I, 1, kiter + 1);
+        s_use_hint = FAST && kiter >= 1 && I->hint_bad != nullptr &&
+                     __ldcg(&I->hint_bad[2 * side + ((kiter - 1) & 1)]) == 0;
+      }
+    }
     __syncthreads();
     if (!s_flag) continue;
     __threadfence();
 
-    const double eps = eps_of(I, kiter);
-    const double inv_eps = 1.0 / eps;
-    const bool use_hint = FAST && kiter >= 1 && I->hint_bad != nullptr &&
-                          __ldcg(&I->hint_bad[2 * side + ((kiter - 1) & 1)]) == 0;
-    const double lam = I->lambda;
-    const double inv_lam = 1.0 / lam;
-    const double inv_eps1 = row_inv_eps(I, kiter + 1);  // the next row sweep's, for the column pack
-    const double inv_row = row_inv_eps(I, kiter);
-    // hints predict this side's next log-sum-exp: scale by the ratio of its temperatures
-    const double hint_ratio = side == 0 ? row_inv_eps(I, kiter + 1) / inv_row : eps / eps_of(I, kiter + 1);
-    // offsets of the pack this sweep read (the other side's) for this and the next iteration, and
-    // of the pack this epilogue writes
-    const double off_q = pack_offset(I, 1 - side, kiter);
-    const double off_q1 = pack_offset(I, 1 - side, kiter + 1);
-    const double off_w = side == 0 ? pack_offset(I, 0, kiter) : pack_offset(I, 1, kiter + 1);
     double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     bool bad = false;
     bool hmiss = false;  // a stored hint missed this sweep's log-sum-exp by more than kHintTol
     float* const hint = UPDATE ? I->hint[side] : nullptr;
+    // Points of this thread in the epilogue: R adjacent ones in the fast sweeps (their (shift, sum)
+    // partials come in pairs, one 16-byte load per pair and split), else the sweep's own layout.
+    auto ep_point = [&](int r) -> int {
+      return FAST ? item.pblk * (kThreads * R) + R * tid + r : item.pblk * (kThreads * R) + r * kThreads + tid;
+    };
+    // The point block's merge waits on L2 for its split partials, and it is on the critical path of
+    // the instance's phase: every round loads a batch of splits of all the thread's points before
+    // merging them (about 32 registers of loads in flight).  Each point's splits are still merged one
+    // by one in index order (a fixed order keeps the result deterministic).
+    // FP32 partials are merged in FP32: exact power-of-two rescaling and Kahan sums (B300's FP64
+    // pipe is slow, and an instance can have tens of split partials per point).
+    float mxf[R], Sf[R], Sc[R], Nf[R], Nc[R];
+    // per-point state the epilogue reads, loaded before the merge so that its latency overlaps it
+    double st_a[R], st_b[R], st_c[R], st_d[R];
+    float st_h[R];
+    if constexpr (MODE != kSweepF64) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        mxf[r] = -INFINITY;
+        Sf[r] = Sc[r] = Nf[r] = Nc[r] = 0.0f;
+      }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int p = item.pblk * (kThreads * R) + r * kThreads + tid;
+      const int p = ep_point(r);
+      st_a[r] = st_b[r] = st_c[r] = st_d[r] = 0.0;
+      st_h[r] = 0.0f;
+      if (p < np) {
+        if (hint != nullptr) st_h[r] = __ldcg(&hint[p]);
+        if (side == 0) {
+          st_a[r] = I->xn2[p];
+          st_b[r] = I->log_a[p];
+          st_c[r] = __ldcg(&I->log_alpha[p]);
+        } else {
+          st_a[r] = I->yn2[p];
+          st_b[r] = I->log_b[p];
+          st_c[r] = UPDATE ? __ldcg(&I->log_beta_tilde_next[p]) : __ldcg(&I->log_beta_tilde[p]);
+          if (UPDATE) st_d[r] = __ldcg(&I->log_beta[p]);
+        }
+      }
+    }
+    // one partial (m, s, n) into the running merge of point r: splits must come in index order
+    auto merge_one = [&](int r, bool first, float ms, float sv, float nv) {
+      if (first) {
+        mxf[r] = ms;
+        Sf[r] = sv;
+        Nf[r] = nv;
+      } else if (ms > mxf[r]) {
+        const float f = exp2_neg_int(ms - mxf[r]);
+        Sf[r] *= f;
+        Sc[r] *= f;
+        Nf[r] *= f;
+        Nc[r] *= f;
+        mxf[r] = ms;
+        kahan_add(Sf[r], Sc[r], sv);
+        if (accn) kahan_add(Nf[r], Nc[r], nv);
+      } else {
+        const float f = exp2_neg_int(mxf[r] - ms);
+        kahan_add(Sf[r], Sc[r], sv * f);
+        if (accn) kahan_add(Nf[r], Nc[r], nv * f);
+      }
+    };
+    if constexpr (FAST) {
+      // (shift, sum) partials of the thread's R adjacent points: R / 2 16-byte loads per split
+      // (one 8-byte load when R = 1); the row stride keeps every pair aligned
+      constexpr int kW = R >= 2 ? R / 2 : 1;          // loads per split
+      constexpr int kB = R >= 2 ? 4 / kW : 8;         // splits per round (more spill registers into the sweep)
+      const size_t pst = part_stride<MODE>(np);
+      const int p0 = ep_point(0);
+      const float* pf = reinterpret_cast<const float*>(I->part);
+      for (int s0 = 0; s0 < splits; s0 += kB) {
+        float4 q[kB][kW];
+#pragma unroll
+        for (int u = 0; u < kB; ++u)
+#pragma unroll
+          for (int w = 0; w < kW; ++w) {
+            if (p0 < np && s0 + u < splits) {
+              const float* a = pf + 2 * ((size_t)(s0 + u) * pst + p0 + 2 * w);
+              if constexpr (R >= 2) {
+                q[u][w] = __ldcg(reinterpret_cast<const float4*>(a));
+              } else {
+                const float2 v = __ldcg(reinterpret_cast<const float2*>(a));
+                q[u][w] = make_float4(v.x, v.y, 0.0f, 0.0f);
+              }
+            }
+          }
+#pragma unroll
+        for (int u = 0; u < kB; ++u) {
+          if (s0 + u >= splits) break;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if (p0 + r >= np) continue;
+            const float4 v = q[u][r / 2];
+            const float ms = (r & 1) ? v.z : v.x;
+            const float sv = (r & 1) ? v.w : v.y;
+            merge_one(r, s0 + u == 0, ms, sv, 0.0f);
+          }
+        }
+      }
+    } else if constexpr (MODE != kSweepF64) {
+      constexpr int kMergeBatch = R >= 2 ? 4 : 8;
+      for (int s0 = 0; s0 < splits; s0 += kMergeBatch) {
+        Part pr[R][kMergeBatch];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int p = ep_point(r);
+#pragma unroll
+          for (int u = 0; u < kMergeBatch; ++u)
+            if (p < np && s0 + u < splits) pr[r][u] = load_part(&part[(size_t)(s0 + u) * np + p]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int p = ep_point(r);
+          if (p >= np) continue;
+#pragma unroll
+          for (int u = 0; u < kMergeBatch; ++u) {
+            if (s0 + u >= splits) break;
+            merge_one(r, s0 + u == 0, pr[r][u].x, pr[r][u].y, part_z(pr[r][u]));
+          }
+        }
+      }
+    }
+    // the epilogue's scalars (read after the merge, which needs the registers)
+    const double eps = s_ep[0];
+    const double inv_eps = s_ep[1];
+    const bool use_hint = s_use_hint != 0;
+    const double lam = I->lambda;
+    const double inv_lam = s_ep[2];
+    const double inv_eps1 = s_ep[3];
+    const double inv_row = s_ep[4];
+    const double hint_ratio = s_ep[5];
+    const double off_q = s_ep[6];
+    const double off_q1 = s_ep[7];
+    const double off_w = s_ep[8];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int p = ep_point(r);
       if (p >= np) continue;
       // merge the splits in index order: a fixed order keeps the result deterministic
       double mx, S, N;
@@ -953,41 +1129,9 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
           }
         }
       } else {
-        // FP32 partials merged in FP32: exact power-of-two rescaling and Kahan sums (B300's FP64
-        // pipe is slow, and an instance can have tens of split partials per point)
-        float mxf = -INFINITY, Sf = 0.0f, Sc = 0.0f, Nf = 0.0f, Nc = 0.0f;
-        for (int s0 = 0; s0 < splits; s0 += 4) {
-          Part pr[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (s0 + u < splits) pr[u] = load_part(&part[(size_t)(s0 + u) * np + p]);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (s0 + u >= splits) break;
-            const float ms = pr[u].x;
-            if (s0 + u == 0) {
-              mxf = ms;
-              Sf = pr[u].y;
-              Nf = pr[u].z;
-            } else if (ms > mxf) {
-              const float f = exp2_neg_int(ms - mxf);
-              Sf *= f;
-              Sc *= f;
-              Nf *= f;
-              Nc *= f;
-              mxf = ms;
-              kahan_add(Sf, Sc, pr[u].y);
-              if (accn) kahan_add(Nf, Nc, pr[u].z);
-            } else {
-              const float f = exp2_neg_int(mxf - ms);
-              kahan_add(Sf, Sc, pr[u].y * f);
-              if (accn) kahan_add(Nf, Nc, pr[u].z * f);
-            }
-          }
-        }
-        mx = (double)mxf;
-        S = (double)Sf - (double)Sc;
-        N = (double)Nf - (double)Nc;
+        mx = (double)mxf[r];
+        S = (double)Sf[r] - (double)Sc[r];
+        N = (double)Nf[r] - (double)Nc[r];
       }
       double lse2;
       if constexpr (FAST) {
@@ -996,7 +1140,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
         lse2 = mx + log2(S);
       }
       if (hint != nullptr) {
-        const float e = __ldcg(&hint[p]);
+        const float e = st_h[r];
         const float l = (float)lse2;
         hmiss |= kiter == 0 || !(fabsf(e - l) <= kHintTol);
         bad |= use_hint && e - l > kHintGuard;  // flushed terms could matter: reject the sweep
@@ -1005,43 +1149,45 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       lse2 += off_q;  // the sweep ran on h - G
       // state written by other CTAs of this launch (earlier phases) is read through L2
       if (side == 0) {
-        const double lse = lse2 * kLn2 - I->xn2[p] * inv_row;
-        double lah = I->log_a[p] - lse;
-        if (I->alg == kAlgDAS && kiter >= 2) lah += __ldcg(&I->log_alpha[p]) / (double)kiter;  // theta_k = 1/k
+        const double xn2 = st_a[r], la_old = st_c[r];
+        const double lse = lse2 * kLn2 - xn2 * inv_row;
+        double lah = st_b[r] - lse;
+        if (I->alg == kAlgDAS && kiter >= 2) lah += la_old / (double)kiter;  // theta_k = 1/k
         bad |= !isfinite(lah);
         I->log_alpha_hat[p] = lah;
-        I->log_alpha[p] = (1.0 - lam) * __ldcg(&I->log_alpha[p]) + lam * lah;
-        store_h(I->xpack, p, I->d, (lah - I->xn2[p] * inv_eps) * kLog2e - off_w);
+        I->log_alpha[p] = (1.0 - lam) * la_old + lam * lah;
+        store_h(I->xpack, p, I->d, (lah - xn2 * inv_eps) * kLog2e - off_w);
         if constexpr (CERT) {
           const double f = eps * lah;
           I->f_cur[p] = f;
           acc0 += I->a[p] * f;
         }
       } else {
-        const double lse = lse2 * kLn2 - I->yn2[p] * inv_eps;  // d_j of Algorithm 2
+        const double yn2 = st_a[r];
+        const double lse = lse2 * kLn2 - yn2 * inv_eps;  // d_j of Algorithm 2
         double lbh;
         double t;
         if constexpr (UPDATE) {
-          lbh = I->log_b[p] - lse;
+          lbh = st_b[r] - lse;
           bad |= !isfinite(lbh);
-          t = __ldcg(&I->log_beta_tilde_next[p]);
+          t = st_c[r];
           I->log_beta_tilde[p] = t;
-          const double bold = __ldcg(&I->log_beta[p]);
+          const double bold = st_d[r];
           const double bnew = (1.0 - lam) * bold + lam * lbh;
           I->log_beta_prev[p] = bold;
           I->log_beta[p] = bnew;
           I->log_beta_hat[p] = lbh;
           const double tn = alg_momentum(I->alg) ? bnew + (bnew - bold) * inv_lam : bnew;
           I->log_beta_tilde_next[p] = tn;
-          store_h(I->ypack, p, I->d, (tn - I->yn2[p] * inv_eps1) * kLog2e - off_w);
+          store_h(I->ypack, p, I->d, (tn - yn2 * inv_eps1) * kLog2e - off_w);
         } else {
           lbh = __ldcg(&I->log_beta_hat[p]);
-          t = __ldcg(&I->log_beta_tilde[p]);
+          t = st_c[r];
         }
         if constexpr (CERT) {
           const double sj = exp(t + lse);
           const double mu = I->kappa * N / S;
-          const double gj = eps * (lbh - I->log_b[p]);
+          const double gj = eps * (lbh - st_b[r]);
           I->g_cur[p] = gj;
           acc0 += I->b[p] * gj;
           acc1 += sj * mu;
