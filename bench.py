@@ -161,7 +161,7 @@ def combine_over_ranks(td, device, t_step, entries, e2e_t, e2e_entries):
             max(float(g[2]) for g in gathered), sum(float(g[3]) for g in gathered))
 
 
-FAST_DRAM_BYTES_PER_ENTRY = (0.644293888e9 + 2.491339e9) / 4.52e11
+FAST_DRAM_BYTES_PER_ENTRY = (0.454266368e9 + 1.922718e9) / 4.52e11
 
 
 def make_stream(args, rank: int):
@@ -615,7 +615,7 @@ def run_ours(args, rank: int, world: int):
     ttg = results[-1]["ttg"]
     fast_n, fast_e, fast_ms = kst[0]  # the fast iterations' launches (row and column sweeps)
     # DRAM bytes per implicit entry of the persistent fast launch, from one ncu capture of a serving
-    # chunk (dram__bytes_read + write: 3.14 GB over 4.52e11 entries); the traffic is split partials
+    # chunk (dram__bytes_read + write: 2.38 GB over 4.52e11 entries); the traffic is split partials
     # written back from L2, which grow with the entries, so it is scaled to this run's average launch
     traffic = FAST_DRAM_BYTES_PER_ENTRY * fast_e / max(fast_n, 1)
     achieved = fast_e / (fast_ms / 1e3) if fast_ms > 0 else None
@@ -663,7 +663,7 @@ def run_ours(args, rank: int, world: int):
         "launch_breakdown": launch_breakdown,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "entries/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "traffic_basis": "bytes per launch: 6.9e-3 B/entry from an ncu capture of one serving chunk, "
+                     "traffic_basis": "bytes per launch: 5.3e-3 B/entry from an ncu capture of one serving chunk, "
                                       "scaled by the entries of this run's average launch",
                      "kernel": "fast sweeps (one launch per chunk: row and column sweeps of every instance)",
                      "launches": fast_n,

@@ -95,7 +95,7 @@ int g_plan[4][5][2] = {};  // [d][mode] -> {R, CH}; R = 0: built-in
 static void builtin_tile(int d, int mode, int* R, int* ch) {
   static const int kPlan[3][5][2] = {
       {{2, 16}, {2, 8}, {2, 8}, {2, 16}, {2, 16}},  // d = 1
-      {{2, 16}, {1, 8}, {1, 8}, {4, 16}, {2, 16}},  // d = 2
+      {{4, 16}, {1, 8}, {1, 8}, {4, 16}, {2, 16}},  // d = 2
       {{4, 8}, {1, 8}, {2, 8}, {2, 16}, {4, 16}},   // d = 3
   };
   const int di = (d >= 1 && d <= 3) ? d - 1 : 1;

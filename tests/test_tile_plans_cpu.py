@@ -6,11 +6,11 @@ P = pytest.importorskip("paper_2609_33814_b300")
 
 def test_plan_table_set_get_reset_and_validation():
     base = P.get_tile_plan(2, "mufu")
-    assert base == (2, 16)                       # built-in: the autotuner's choice on B300
+    assert base == (4, 16)                       # built-in: the measured choice on B300
     assert P.get_tile_plan(3, "mufu") == (4, 8)
     assert P.get_tile_plan(2, "comp") == (1, 8)
-    P.set_tile_plan(2, "mufu", 4, 8)
-    assert P.get_tile_plan(2, "mufu") == (4, 8)
+    P.set_tile_plan(2, "mufu", 2, 8)
+    assert P.get_tile_plan(2, "mufu") == (2, 8)
     assert P.get_tile_plan(3, "mufu") == (4, 8)  # other entries untouched
     P.set_tile_plan(2, "mufu", 0, 0)
     assert P.get_tile_plan(2, "mufu") == base
