@@ -321,7 +321,8 @@ void ot_serve_destroy(ot_server* sv);
  * that cannot allocate device memory (code running under a runtime or plugin host that owns all
  * device allocations and forbids libraries from calling cudaMalloc).  It computes
  *     log_alpha_hat[i] = log_r[i] - LSE_j( log_bt[j] - kappa ||x_i - y_j||^2 / eps )
- * with the same FP32 kernel as ot_step's fast row sweep, and allocates nothing: every buffer it
+ * with the FP32 sweep kernel of ot_step's fast iterations (its one-point-per-thread, 16-column-chunk
+ * instantiation, whatever the tile plan), and allocates nothing: every buffer it
  * needs beyond its arguments lives in a fixed scratch array of about 3.2 MB inside the library,
  * which every GPU that loads the library holds until the process exits.
  *   - x (n x d floats), y (m x d floats), log_r (n doubles), log_bt (m doubles) are device inputs;
