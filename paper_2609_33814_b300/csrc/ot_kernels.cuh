@@ -74,7 +74,8 @@ struct Inst {
   double* log_beta_tilde_next;   // beta-tilde^{k} for the next iteration (packed into ypack)
   double* f_cur;                 // certificate potentials of the latest certificate iteration
   double* g_cur;
-  void* part;                    // split partials (float4, or PartF64 in FP64 sweeps, per point and split)
+  void* part;                    // split partials per point and split: float2 (shift, sum) in the fast sweeps
+                                 // (rows of part_stride points), float4 in the compensated ones, PartF64 in FP64
   unsigned* cnt;                 // per point-block arrival counters (sized for R = 1)
   unsigned* done;                // per-instance epilogue counter
   double* blk;                   // certificate partial sums: pblk_x row blocks, then 3 per column block
