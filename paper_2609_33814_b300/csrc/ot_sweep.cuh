@@ -970,8 +970,8 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
     };
     // The point block's merge waits on L2 for its split partials, and it is on the critical path of
     // the instance's phase: every round loads a batch of splits of all the thread's points before
-    // merging them (about 32 registers of loads in flight).  Each point's splits are still merged one
-    // by one in index order (a fixed order keeps the result deterministic).
+    // merging them (16 registers of loads in flight).  Each point's splits are still merged one by one
+    // in index order (a fixed order keeps the result deterministic).
     // FP32 partials are merged in FP32: exact power-of-two rescaling and Kahan sums (B300's FP64
     // pipe is slow, and an instance can have tens of split partials per point).
     float mxf[R], Sf[R], Sc[R], Nf[R], Nc[R];
@@ -1029,7 +1029,7 @@ __global__ void __launch_bounds__(kThreads, sweep_min_blocks<D, R, MODE>()) swee
       // (shift, sum) partials of the thread's R adjacent points: R / 2 16-byte loads per split
       // (one 8-byte load when R = 1); the row stride keeps every pair aligned
       constexpr int kW = R >= 2 ? R / 2 : 1;          // loads per split
-      constexpr int kB = R >= 2 ? 4 / kW : 8;         // splits per round (more spill registers into the sweep)
+      constexpr int kB = R >= 2 ? 4 / kW : 8;         // splits per round (a larger batch spills into the sweep)
       const size_t pst = part_stride<MODE>(np);
       const int p0 = ep_point(0);
       const float* pf = reinterpret_cast<const float*>(I->part);
